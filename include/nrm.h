@@ -1,0 +1,190 @@
+/*
+ * nrm.h - C ABI of the GB300 (sm_103a) surface-normal library.
+ *
+ * Method: Moradi, Memarmoghadam and Laurendeau, "Fast, Accurate and Object
+ * Boundary-Aware Surface Normal Estimation from Depth Maps", arXiv 2209.08241.
+ *
+ * For every pixel of an organised depth map the library computes the
+ * multi-direction normal of Section 3.1 (the average of four perpendicular
+ * tangent-pair cross products), evaluated through its reformulation as one
+ * cross product 1/4 s24 x s35 in the closed form of Eq. 4-6:
+ *   n_x = -alpha/(4 f_y) (d3 + d5)(d2 - d4)
+ *   n_y = -alpha/(4 f_x) (d2 + d4)(d3 - d5)
+ *   n_z = -u1 n_x - v1 n_y + alpha^2/(4 f_x f_y) (d2 + d4)(d3 + d5)
+ * with u1 = (col - cx)/fx, v1 = (row - cy)/fy (Section 2, definitions below
+ * Eq. 3), neighbours 2/4 at +-alpha along the column axis and 3/5 at +-alpha
+ * along the row axis (Fig. 2). It then normalises n and removes normals at
+ * depth discontinuities by thresholding the length statistic of Section 3.2
+ * (Eq. "veclength"), applying the mask to the normal map (Section 4, Fig. 8).
+ *
+ * Conventions (the paper is silent on them):
+ *   - A pixel is invalid when any of its five stencil depths lies outside the
+ *     image or is not a positive finite number (uint16: raw value 0).
+ *   - Mask statistic: NRM_MASK_RAW thresholds r = ||n|| (the paper's literal
+ *     statistic, in m^2); NRM_MASK_SECANT thresholds r ||ray|| / (n . ray) with
+ *     ray = (u1, v1, 1), which equals 1/cos of the angle between the normal and
+ *     the viewing ray and does not depend on depth, alpha or focal length.
+ *   - A pixel is valid iff stat <= tau. Masked pixels get the normal (0,0,0,0)
+ *     and mask byte 0; valid pixels get mask byte 1.
+ *   - Sign: the paper's normal points away from the camera (n . P1 > 0);
+ *     orient_to_camera = 1 negates it.
+ *
+ * Memory and ownership: every depth, normal, mask and gradient pointer passed
+ * to this library is a DEVICE pointer owned by the caller. Normals are stored
+ * as 4 components per pixel (x, y, z, 0): float32 (16 B/px) or IEEE half
+ * (8 B/px). The mask is one uint8 per pixel. All images are row-major.
+ * A handle owns only small device state: per-frame descriptors and TMA tensor
+ * maps, a status word and captured CUDA graphs.
+ *
+ * Errors: every call returns an nrm_status. Arguments are checked on the host
+ * before anything is launched; a rejected call launches nothing and sets a
+ * thread-local message readable with nrm_last_error(). Launches are
+ * asynchronous on the caller's stream (NULL = the legacy default stream).
+ * Device-side failures (a bounded wait that ran out) are written to the
+ * handle's status word and reported by nrm_sync_status().
+ *
+ * Threading: a handle may be used from one host thread at a time.
+ */
+#ifndef NRM_H_
+#define NRM_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NRM_API __attribute__((visibility("default")))
+#else
+#define NRM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NRM_OK = 0,
+  NRM_ERR_INVALID_ARG = 1, /* bad pointer, size, pitch or parameter */
+  NRM_ERR_UNSUPPORTED = 2, /* valid but outside what the kernels support */
+  NRM_ERR_CUDA = 3,        /* a CUDA runtime call failed (see nrm_last_error) */
+  NRM_ERR_OOM = 4,         /* a device or pinned allocation failed */
+  NRM_ERR_TIMEOUT = 5,     /* a bounded device wait ran out */
+  NRM_ERR_NO_DEVICE = 6    /* no CUDA device is visible */
+} nrm_status;
+
+/* Pinhole intrinsics in pixels (Section 2: f_x, f_y, o_x, o_y). */
+typedef struct {
+  double fx, fy, cx, cy;
+} nrm_intrinsics;
+
+typedef enum { NRM_IN_F32_M = 0, NRM_IN_U16_MM = 1 } nrm_in_dtype;
+typedef enum { NRM_OUT_F32X4 = 0, NRM_OUT_F16X4 = 1 } nrm_out_dtype;
+typedef enum { NRM_MASK_RAW = 0, NRM_MASK_SECANT = 1 } nrm_mask_mode;
+
+/* Largest pixel distance alpha the kernels accept. */
+#define NRM_MAX_ALPHA 16
+
+typedef struct {
+  int alpha;            /* pixel distance alpha, 1..NRM_MAX_ALPHA (Section 3.1) */
+  int mask_mode;        /* nrm_mask_mode */
+  float tau;            /* threshold: valid iff stat <= tau; tau >= 0 (may be +inf) */
+  float depth_scale;    /* metres per uint16 unit (default 0.001) */
+  int in_dtype;         /* nrm_in_dtype of nrm_estimate / nrm_backward input */
+  int out_dtype;        /* nrm_out_dtype of the normal map */
+  int orient_to_camera; /* 0 = paper sign (default), 1 = negated */
+} nrm_params;
+
+/* Defaults: alpha 2, SECANT, tau 12, depth_scale 0.001, f32 in, f32x4 out. */
+NRM_API void nrm_default_params(nrm_params* p);
+
+typedef struct nrm_handle nrm_handle;
+
+/* One frame of a batch. Pitches are in elements of the respective buffer:
+ * depth_pitch in depth elements (>= W); out_pitch in pixels for both the normal
+ * map and the mask (>= W). */
+typedef struct {
+  const void* depth;
+  void* normals;
+  uint8_t* valid;
+  int H, W;
+  long long depth_pitch;
+  long long out_pitch;
+  nrm_intrinsics K;
+  int in_dtype;
+} nrm_frame;
+
+/* Creates a handle for H x W frames with intrinsics K (used by nrm_estimate and
+ * nrm_backward; batched calls carry their own sizes and intrinsics). H = W = 0
+ * (K may then be NULL) makes a handle for batched calls only. p = NULL takes
+ * the defaults. Allocates the handle's device state on the current device. */
+NRM_API int nrm_create(const nrm_intrinsics* K, int H, int W, const nrm_params* p, nrm_handle** out);
+
+/* Releases the handle and its device state. Waits for its pending work. */
+NRM_API void nrm_destroy(nrm_handle* h);
+
+/* Single frame, one plain launch (one CTA per tile, TMA-staged halo tiles).
+ * depth: H x W (dense, pitch W) of the handle's in_dtype; normals: H x W x 4
+ * (dense) of the handle's out_dtype; valid: H x W bytes (dense). */
+NRM_API int nrm_estimate(nrm_handle* h, const void* depth, void* normals, uint8_t* valid,
+                 void* cuda_stream);
+
+/* n frames of any sizes, intrinsics and input dtypes in ONE persistent launch
+ * over a (frame, tile) work list, replayed from a CUDA graph that the handle
+ * captured once (a descriptor upload node followed by the kernel node). The
+ * handle's alpha, mask mode, tau, depth_scale, out_dtype and orientation apply
+ * to all frames. n = 0 is a no-op. The frames' buffers must not overlap. The
+ * host may return before the GPU has read the descriptors; the handle keeps a
+ * ring of descriptor slots and blocks only when every slot is still in use. */
+NRM_API int nrm_estimate_batched(nrm_handle* h, const nrm_frame* frames, int n, void* cuda_stream);
+
+/* Adjoint of nrm_estimate for float32 depth (derivatives of Eq. 4-6 and of the
+ * normalisation), with the mask held fixed:
+ *   grad_depth[q] = sum over valid p whose stencil holds q of
+ *                   g[p] . d(n_hat[p]) / d(depth[q]),
+ * g = grad_normals, H x W x 4 float32 (the 4th component is ignored).
+ * valid: the mask nrm_estimate produced. Deterministic (gather, no atomics).
+ * Returns NRM_ERR_UNSUPPORTED for a uint16 handle. */
+NRM_API int nrm_backward(nrm_handle* h, const void* depth, const float* grad_normals,
+                 const uint8_t* valid, float* grad_depth, void* cuda_stream);
+
+/* Waits for the handle's work, returns the device status word (NRM_OK or the
+ * first device-side error since the last call) and clears it. */
+NRM_API int nrm_sync_status(nrm_handle* h);
+
+/* Launch geometry of the forward kernels. tile_x in {64, 128, 256}, tile_y in
+ * {4, 8, 16, 32}, threads in {128, 256, 512}, stages in {2, 3, 4} (persistent
+ * kernel only), ctas_per_sm 0 = as many as fit. */
+typedef struct {
+  int tile_x, tile_y, threads, stages, ctas_per_sm;
+} nrm_tile_config;
+
+NRM_API int nrm_get_config(const nrm_handle* h, nrm_tile_config* cfg);
+NRM_API int nrm_set_config(nrm_handle* h, const nrm_tile_config* cfg);
+
+/* Times every supported configuration on the given batch (which must stay
+ * valid during the call; outputs are overwritten), keeps the fastest in the
+ * handle and records it in the JSON cache file cache_path (NULL = no file),
+ * keyed by GPU name, SM count, frame-size class, dtypes and alpha. If the
+ * cache already holds the key, loads it without timing. Synchronous. */
+NRM_API int nrm_autotune(nrm_handle* h, const nrm_frame* frames, int n, void* cuda_stream,
+                 const char* cache_path);
+
+/* Kernel-time statistics of batched launches: CUDA events recorded around the
+ * kernel node inside the graph. Enabling timing adds two event nodes. */
+typedef struct {
+  long long launches; /* completed timed launches */
+  double kernel_ms;   /* sum of their kernel durations */
+  long long tiles;    /* tiles processed by them */
+} nrm_stats;
+
+NRM_API int nrm_enable_timing(nrm_handle* h, int enable);
+NRM_API int nrm_get_stats(nrm_handle* h, nrm_stats* out); /* waits for pending launches */
+NRM_API int nrm_reset_stats(nrm_handle* h);
+
+NRM_API const char* nrm_status_string(int status);
+NRM_API const char* nrm_last_error(void); /* thread-local, "" if none */
+NRM_API const char* nrm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NRM_H_ */

@@ -1,0 +1,295 @@
+"""GB300-native boundary-aware surface normals from depth maps (arXiv 2209.08241).
+
+A thin Python layer over the C ABI of ``libnrm.so`` (include/nrm.h). Every
+step of the method runs in the library's CUDA kernels; this module only
+allocates output tensors with torch, passes device pointers and the current
+CUDA stream, and raises on a non-zero status. There is no CPU fallback: on a
+machine without the built library or a GPU every call raises.
+
+    est = NormalEstimator((fx, fy, cx, cy), H, W, alpha=2)
+    normals, mask = est(depth)              # depth: (H, W) float32 or uint16 CUDA tensor
+
+    batch = BatchedEstimator(alpha=2)
+    outs = batch([(depth0, K0), (depth1, K1), ...])    # one persistent launch
+
+    n = estimate_normals(depth, K)          # differentiable (float32 depth)
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+from typing import Sequence
+
+import torch
+
+from . import _lib
+from ._lib import (NRM_IN_F32_M, NRM_IN_U16_MM, NRM_MASK_RAW, NRM_MASK_SECANT, NRM_MAX_ALPHA,
+                   NRM_OUT_F16X4, NRM_OUT_F32X4, NrmError)
+
+__all__ = ["NormalEstimator", "BatchedEstimator", "NormalParams", "NrmError", "estimate_normals",
+           "NormalsFunction", "MASK_RAW", "MASK_SECANT", "version"]
+
+MASK_RAW = NRM_MASK_RAW
+MASK_SECANT = NRM_MASK_SECANT
+
+
+@dataclass
+class NormalParams:
+    """Mirror of ``nrm_params``. mask_mode: "secant" (default) or "raw"."""
+    alpha: int = 2
+    mask_mode: str = "secant"
+    tau: float = 12.0
+    depth_scale: float = 0.001
+    out_dtype: str = "f32"          # "f32" (float4 per pixel) or "f16" (half4)
+    orient_to_camera: bool = False
+
+    def to_c(self, in_dtype: int) -> _lib.Params:
+        p = _lib.Params()
+        p.alpha = int(self.alpha)
+        p.mask_mode = {"secant": NRM_MASK_SECANT, "raw": NRM_MASK_RAW}[self.mask_mode]
+        p.tau = float(self.tau)
+        p.depth_scale = float(self.depth_scale)
+        p.in_dtype = int(in_dtype)
+        p.out_dtype = {"f32": NRM_OUT_F32X4, "f16": NRM_OUT_F16X4}[self.out_dtype]
+        p.orient_to_camera = int(bool(self.orient_to_camera))
+        return p
+
+    @property
+    def torch_out_dtype(self) -> torch.dtype:
+        return torch.float32 if self.out_dtype == "f32" else torch.float16
+
+
+def version() -> str:
+    return _lib.load().nrm_version().decode()
+
+
+def _in_dtype(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return NRM_IN_F32_M
+    if t.dtype == torch.uint16:
+        return NRM_IN_U16_MM
+    raise TypeError(f"depth must be float32 (metres) or uint16 (depth_scale units), got {t.dtype}")
+
+
+def _stream_ptr(stream: torch.cuda.Stream | None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _intr(K) -> _lib.Intrinsics:
+    fx, fy, cx, cy = (float(v) for v in K)
+    return _lib.Intrinsics(fx, fy, cx, cy)
+
+
+def _check_cuda(t: torch.Tensor, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+
+
+class _Handle:
+    def __init__(self, K, H: int, W: int, params: NormalParams, in_dtype: int, device=None):
+        self.lib = _lib.load()
+        self.params = params
+        self.in_dtype = in_dtype
+        self.H, self.W = int(H), int(W)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        h = ctypes.c_void_p()
+        c_params = params.to_c(in_dtype)
+        with torch.cuda.device(self.device):
+            kp = ctypes.byref(_intr(K)) if K is not None else None
+            _lib.check(self.lib.nrm_create(kp, self.H, self.W, ctypes.byref(c_params),
+                                           ctypes.byref(h)), "nrm_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.nrm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # Introspection and tuning ------------------------------------------
+    def config(self) -> dict:
+        c = _lib.TileConfig()
+        _lib.check(self.lib.nrm_get_config(self.h, ctypes.byref(c)), "nrm_get_config")
+        return {k: getattr(c, k) for k, _ in c._fields_}
+
+    def set_config(self, tile_x=128, tile_y=16, threads=256, stages=3, ctas_per_sm=0):
+        c = _lib.TileConfig(tile_x, tile_y, threads, stages, ctas_per_sm)
+        _lib.check(self.lib.nrm_set_config(self.h, ctypes.byref(c)), "nrm_set_config")
+
+    def sync_status(self):
+        _lib.check(self.lib.nrm_sync_status(self.h), "nrm_sync_status")
+
+    def enable_timing(self, on: bool = True):
+        _lib.check(self.lib.nrm_enable_timing(self.h, int(on)), "nrm_enable_timing")
+
+    def stats(self) -> dict:
+        s = _lib.Stats()
+        _lib.check(self.lib.nrm_get_stats(self.h, ctypes.byref(s)), "nrm_get_stats")
+        return {"launches": s.launches, "kernel_ms": s.kernel_ms, "tiles": s.tiles}
+
+    def reset_stats(self):
+        _lib.check(self.lib.nrm_reset_stats(self.h), "nrm_reset_stats")
+
+
+class NormalEstimator(_Handle):
+    """Fixed-size single-frame estimator (one plain launch per call).
+
+    ``in_dtype`` is "f32" (metres) or "u16" (units of ``depth_scale``)."""
+
+    def __init__(self, K, H: int, W: int, params: NormalParams | None = None,
+                 in_dtype: str = "f32", device=None, **kw):
+        params = params or NormalParams(**kw)
+        super().__init__(K, H, W, params, {"f32": NRM_IN_F32_M, "u16": NRM_IN_U16_MM}[in_dtype], device)
+        self.K = tuple(float(v) for v in K)
+
+    def new_outputs(self):
+        n = torch.empty((self.H, self.W, 4), dtype=self.params.torch_out_dtype, device=self.device)
+        m = torch.empty((self.H, self.W), dtype=torch.uint8, device=self.device)
+        return n, m
+
+    def estimate(self, depth: torch.Tensor, normals: torch.Tensor | None = None,
+                 valid: torch.Tensor | None = None, stream=None):
+        """Writes the (H, W, 4) normal map and (H, W) uint8 mask; returns both."""
+        _check_cuda(depth, "depth")
+        if tuple(depth.shape) != (self.H, self.W) or not depth.is_contiguous():
+            raise ValueError(f"depth must be a contiguous ({self.H}, {self.W}) tensor")
+        if _in_dtype(depth) != self.in_dtype:
+            raise TypeError("depth dtype does not match the estimator's in_dtype")
+        if normals is None or valid is None:
+            normals, valid = self.new_outputs()
+        _lib.check(self.lib.nrm_estimate(self.h, depth.data_ptr(), normals.data_ptr(),
+                                         valid.data_ptr(), _stream_ptr(stream)), "nrm_estimate")
+        return normals, valid
+
+    __call__ = estimate
+
+    def backward(self, depth: torch.Tensor, grad_normals: torch.Tensor, valid: torch.Tensor,
+                 grad_depth: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """dL/d(depth) for upstream dL/d(normals) (H, W, 4) float32, mask fixed."""
+        for t, n in ((depth, "depth"), (grad_normals, "grad_normals"), (valid, "valid")):
+            _check_cuda(t, n)
+            if not t.is_contiguous():
+                raise ValueError(f"{n} must be contiguous")
+        if grad_normals.dtype != torch.float32 or tuple(grad_normals.shape) != (self.H, self.W, 4):
+            raise ValueError("grad_normals must be (H, W, 4) float32")
+        if grad_depth is None:
+            grad_depth = torch.empty((self.H, self.W), dtype=torch.float32, device=self.device)
+        _lib.check(self.lib.nrm_backward(self.h, depth.data_ptr(), grad_normals.data_ptr(),
+                                         valid.data_ptr(), grad_depth.data_ptr(),
+                                         _stream_ptr(stream)), "nrm_backward")
+        return grad_depth
+
+
+def _frame(depth: torch.Tensor, K, normals: torch.Tensor, valid: torch.Tensor) -> _lib.Frame:
+    f = _lib.Frame()
+    f.depth = depth.data_ptr()
+    f.normals = normals.data_ptr()
+    f.valid = valid.data_ptr()
+    f.H, f.W = int(depth.shape[0]), int(depth.shape[1])
+    if depth.numel():
+        f.depth_pitch = int(depth.stride(0))
+        f.out_pitch = int(normals.stride(0) // 4)
+    else:
+        f.depth_pitch = f.out_pitch = f.W
+    f.K = _intr(K)
+    f.in_dtype = _in_dtype(depth)
+    return f
+
+
+class BatchedEstimator(_Handle):
+    """Any number of frames of any sizes, intrinsics and input dtypes per call,
+    processed by one persistent launch replayed from a CUDA graph."""
+
+    def __init__(self, params: NormalParams | None = None, device=None, **kw):
+        params = params or NormalParams(**kw)
+        super().__init__(None, 0, 0, params, NRM_IN_F32_M, device)
+        self._frames = None
+
+    def make_frames(self, items: Sequence, outputs: Sequence | None = None):
+        """ctypes frame array for [(depth, K), ...] with outputs [(normals, valid), ...]
+        (allocated when None). Returns (frames_array, outputs)."""
+        n = len(items)
+        arr = (_lib.Frame * max(n, 1))()
+        outs = []
+        for i, (depth, K) in enumerate(items):
+            _check_cuda(depth, "depth")
+            if depth.dim() != 2 or depth.stride(1) != 1:
+                raise ValueError("each depth must be a 2-D tensor with unit column stride")
+            H, W = depth.shape
+            if outputs is None:
+                nm = torch.empty((H, W, 4), dtype=self.params.torch_out_dtype, device=depth.device)
+                vm = torch.empty((H, W), dtype=torch.uint8, device=depth.device)
+            else:
+                nm, vm = outputs[i]
+            if tuple(nm.shape) != (H, W, 4) or tuple(vm.shape) != (H, W):
+                raise ValueError("outputs must be (H, W, 4) normals and (H, W) valid")
+            if depth.numel() and (nm.stride(2) != 1 or nm.stride(1) != 4 or nm.stride(0) % 4
+                                  or vm.stride(1) != 1 or vm.stride(0) * 4 != nm.stride(0)):
+                raise ValueError("normals (H, W, 4) and valid (H, W) must share the pixel pitch")
+            if nm.dtype != self.params.torch_out_dtype or vm.dtype != torch.uint8:
+                raise TypeError("output dtypes do not match the estimator's out_dtype / uint8")
+            arr[i] = _frame(depth, K, nm, vm)
+            outs.append((nm, vm))
+        return arr, outs
+
+    def run(self, frames_array, n: int, stream=None):
+        _lib.check(self.lib.nrm_estimate_batched(self.h, frames_array, int(n), _stream_ptr(stream)),
+                   "nrm_estimate_batched")
+
+    def __call__(self, items: Sequence, outputs: Sequence | None = None, stream=None):
+        arr, outs = self.make_frames(items, outputs)
+        self.run(arr, len(items), stream)
+        return outs
+
+    def autotune(self, items: Sequence, outputs: Sequence | None = None, cache_path: str | None = None,
+                 stream=None) -> dict:
+        arr, _ = self.make_frames(items, outputs)
+        cp = cache_path.encode() if cache_path else None
+        _lib.check(self.lib.nrm_autotune(self.h, arr, len(items), _stream_ptr(stream), cp), "nrm_autotune")
+        return self.config()
+
+
+class NormalsFunction(torch.autograd.Function):
+    """Differentiable normal map of float32 depth: forward = nrm_estimate,
+    backward = nrm_backward (mask held fixed; the mask output has no gradient)."""
+
+    @staticmethod
+    def forward(ctx, depth: torch.Tensor, est: NormalEstimator):
+        depth = depth.contiguous()
+        normals, valid = est.estimate(depth)
+        ctx.est = est
+        ctx.save_for_backward(depth, valid)
+        ctx.mark_non_differentiable(valid)
+        return normals, valid
+
+    @staticmethod
+    def backward(ctx, grad_normals, grad_valid):
+        depth, valid = ctx.saved_tensors
+        if grad_normals is None:
+            return None, None
+        g = grad_normals.contiguous().to(torch.float32)
+        return ctx.est.backward(depth, g, valid), None
+
+
+_estimators: dict = {}
+
+
+def estimate_normals(depth: torch.Tensor, K, params: NormalParams | None = None):
+    """Differentiable (H, W) float32 depth -> ((H, W, 4) normals, (H, W) mask).
+    Handles are cached per (shape, K, params, device)."""
+    params = params or NormalParams()
+    key = (tuple(depth.shape), tuple(float(v) for v in K), repr(params), depth.device.index)
+    est = _estimators.get(key)
+    if est is None:
+        with torch.cuda.device(depth.device):
+            est = NormalEstimator(K, depth.shape[0], depth.shape[1], params,
+                                  in_dtype="f32" if depth.dtype == torch.float32 else "u16")
+        _estimators[key] = est
+    return NormalsFunction.apply(depth, est)

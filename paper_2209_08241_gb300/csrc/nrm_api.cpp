@@ -1,0 +1,781 @@
+// Host side of the C ABI declared in include/nrm.h.
+//
+// Responsibilities: argument validation (nothing is launched on bad input),
+// per-frame descriptors with the Eq. 4-6 constants and TMA tensor maps, the
+// plain per-frame launch, the batched persistent launch replayed from a CUDA
+// graph (descriptor upload node -> [event] -> kernel node -> [event]) over a
+// ring of descriptor slots, the adjoint launch, kernel timing, the device
+// status word and the autotuner with its JSON cache.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "nrm.h"
+#include "nrm_internal.h"
+
+using nrm::FrameDesc;
+using nrm::FwdKernelSet;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(NRM_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver)
+    return fail(NRM_ERR_NO_DEVICE, "%s: %s", what, cudaGetErrorString(e));
+  return fail(NRM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define NRM_CUDA(call, what)                 \
+  do {                                       \
+    cudaError_t e_ = (call);                 \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+// ------------------------------------------------ driver entry point (TMA)
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// Encodes a 2-D tiled map of a depth image with box (box_w x box_h) elements,
+// zero fill outside the image. Returns false if the map cannot be made.
+bool encode_depth_map(CUtensorMap* m, const void* base, int in_dtype, int W, int H, long long pitch,
+                      int box_w, int box_h) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const int eb = in_dtype == NRM_IN_U16_MM ? 2 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch * (cuuint64_t)eb};
+  cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, in_dtype == NRM_IN_U16_MM ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                  2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+bool finite_positive(double v) { return std::isfinite(v) && v != 0.0; }
+
+int pow2_align(uintptr_t v, int cap) {
+  int a = 1;
+  while (a < cap && (v % (uintptr_t)(2 * a)) == 0) a *= 2;
+  return a;
+}
+
+// Fills everything of a FrameDesc except tile_begin. box_* are the halo box
+// for the kernel that will read it. Returns NRM_OK or an error (message set).
+int make_desc(FrameDesc* d, const void* depth, void* normals, uint8_t* valid, int H, int W,
+              long long depth_pitch, long long out_pitch, const nrm_intrinsics& K, int in_dtype,
+              const nrm_params& p, int tile_x, int tile_y, int box_w, int box_h) {
+  std::memset(d, 0, sizeof(*d));
+  d->depth = depth;
+  d->normals = normals;
+  d->valid = valid;
+  d->H = H;
+  d->W = W;
+  d->depth_pitch = depth_pitch;
+  d->out_pitch = out_pitch;
+  d->tiles_x = W > 0 ? (W + tile_x - 1) / tile_x : 0;
+  const double s = in_dtype == NRM_IN_U16_MM ? (double)p.depth_scale : 1.0;
+  const double al = (double)p.alpha;
+  d->a = (float)(al / (4.0 * K.fy) * s * s);
+  d->b = (float)(al / (4.0 * K.fx) * s * s);
+  d->c = (float)(al * al / (4.0 * K.fx * K.fy) * s * s);
+  d->inv_fx = (float)(1.0 / K.fx);
+  d->inv_fy = (float)(1.0 / K.fy);
+  d->cx = (float)K.cx;
+  d->cy = (float)K.cy;
+  d->in_dtype = in_dtype;
+  d->mask_align = valid ? std::min(pow2_align((uintptr_t)valid, 16), pow2_align((uintptr_t)out_pitch, 16)) : 1;
+  const int eb = in_dtype == NRM_IN_U16_MM ? 2 : 4;
+  const bool aligned = ((uintptr_t)depth % 16 == 0) && ((depth_pitch * eb) % 16 == 0) &&
+                       (depth_pitch * eb) < (1LL << 40) && H > 0 && W > 0;
+  d->use_tma = 0;
+  if (aligned && encode_depth_map(&d->tmap, depth, in_dtype, W, H, depth_pitch, box_w, box_h)) d->use_tma = 1;
+  (void)tile_y;
+  return NRM_OK;
+}
+
+int validate_params(const nrm_params& p) {
+  if (p.alpha < 1 || p.alpha > NRM_MAX_ALPHA)
+    return fail(NRM_ERR_UNSUPPORTED, "alpha %d outside 1..%d", p.alpha, NRM_MAX_ALPHA);
+  if (p.mask_mode != NRM_MASK_RAW && p.mask_mode != NRM_MASK_SECANT)
+    return fail(NRM_ERR_INVALID_ARG, "mask_mode %d", p.mask_mode);
+  if (!(p.tau >= 0.0f)) return fail(NRM_ERR_INVALID_ARG, "tau must be >= 0 (got %g)", (double)p.tau);
+  if (!(p.depth_scale > 0.0f) || !std::isfinite(p.depth_scale))
+    return fail(NRM_ERR_INVALID_ARG, "depth_scale must be positive and finite");
+  if (p.in_dtype != NRM_IN_F32_M && p.in_dtype != NRM_IN_U16_MM)
+    return fail(NRM_ERR_INVALID_ARG, "in_dtype %d", p.in_dtype);
+  if (p.out_dtype != NRM_OUT_F32X4 && p.out_dtype != NRM_OUT_F16X4)
+    return fail(NRM_ERR_INVALID_ARG, "out_dtype %d", p.out_dtype);
+  if (p.orient_to_camera != 0 && p.orient_to_camera != 1)
+    return fail(NRM_ERR_INVALID_ARG, "orient_to_camera must be 0 or 1");
+  return NRM_OK;
+}
+
+int validate_intrinsics(const nrm_intrinsics& K) {
+  if (!finite_positive(K.fx) || !finite_positive(K.fy) || !std::isfinite(K.cx) || !std::isfinite(K.cy))
+    return fail(NRM_ERR_INVALID_ARG, "intrinsics must be finite with nonzero fx, fy");
+  return NRM_OK;
+}
+
+constexpr int kSlots = 3;
+constexpr unsigned long long kDefaultTimeoutNs = 2000000000ull;  // 2 s
+
+struct Slot {
+  void* host = nullptr;       // pinned staging of the descriptor block
+  void* dev = nullptr;        // device descriptor block
+  int capacity = 0;           // frames
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t copy_node = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr, done = nullptr;
+  bool graph_timed = false;
+  bool in_flight = false;
+  bool timed_launch = false;
+  int tiles = 0;
+};
+
+}  // namespace
+
+struct nrm_handle {
+  int device = 0;
+  int sm_count = 0;
+  char gpu_name[256] = {0};
+  int H = 0, W = 0;
+  nrm_intrinsics K = {1, 1, 0, 0};
+  nrm_params p;
+  nrm_tile_config cfg = {128, 16, 256, 3, 0};
+  const FwdKernelSet* ks = nullptr;
+  int persistent_grid = 0;
+  int* d_status = nullptr;
+  unsigned long long timeout_ns = kDefaultTimeoutNs;
+  Slot slots[kSlots];
+  int next_slot = 0;
+  bool timing = false;
+  nrm_stats stats = {0, 0.0, 0};
+  cudaEvent_t last_single = nullptr;  // after the latest plain / backward launch
+  std::vector<FrameDesc> scratch_desc;
+};
+
+namespace {
+
+nrm::Globals make_globals(const nrm_handle* h) {
+  nrm::Globals g;
+  g.alpha = h->p.alpha;
+  g.mask_mode = h->p.mask_mode;
+  g.tau2 = std::isinf(h->p.tau) ? INFINITY : h->p.tau * h->p.tau;
+  g.sign = h->p.orient_to_camera ? -1.0f : 1.0f;
+  g.status = h->d_status;
+  g.timeout_ns = h->timeout_ns;
+  return g;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+int set_smem_attr(const void* fn, unsigned bytes) {
+  // Per (kernel, device) maximum already granted.
+  static std::map<std::pair<const void*, int>, unsigned> granted;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto key = std::make_pair(fn, dev);
+  auto it = granted.find(key);
+  if (it != granted.end() && it->second >= bytes) return NRM_OK;
+  NRM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
+           "cudaFuncSetAttribute");
+  granted[key] = bytes;
+  return NRM_OK;
+}
+
+void destroy_slot_graph(Slot& s) {
+  if (s.exec) cudaGraphExecDestroy(s.exec);
+  if (s.graph) cudaGraphDestroy(s.graph);
+  s.exec = nullptr;
+  s.graph = nullptr;
+  s.copy_node = nullptr;
+}
+
+// Waits for a slot's previous launch and folds its kernel time into the stats.
+int retire_slot(nrm_handle* h, Slot& s) {
+  if (!s.in_flight) return NRM_OK;
+  NRM_CUDA(cudaEventSynchronize(s.done), "cudaEventSynchronize");
+  if (s.timed_launch) {
+    float ms = 0.0f;
+    NRM_CUDA(cudaEventElapsedTime(&ms, s.ev_start, s.ev_end), "cudaEventElapsedTime");
+    h->stats.launches += 1;
+    h->stats.kernel_ms += ms;
+    h->stats.tiles += s.tiles;
+  }
+  s.in_flight = false;
+  return NRM_OK;
+}
+
+int retire_all(nrm_handle* h) {
+  for (auto& s : h->slots) {
+    int rc = retire_slot(h, s);
+    if (rc) return rc;
+  }
+  if (h->last_single) NRM_CUDA(cudaEventSynchronize(h->last_single), "cudaEventSynchronize");
+  return NRM_OK;
+}
+
+int configure(nrm_handle* h, const nrm_tile_config& c) {
+  const FwdKernelSet* ks = nrm::fwd_kernel_find(c.tile_x, c.tile_y, c.threads);
+  if (!ks) return fail(NRM_ERR_UNSUPPORTED, "no compiled kernel for tile %dx%d, %d threads", c.tile_x, c.tile_y, c.threads);
+  if (c.stages < 2 || c.stages > 4) return fail(NRM_ERR_UNSUPPORTED, "stages must be 2..4");
+  if (c.ctas_per_sm < 0) return fail(NRM_ERR_INVALID_ARG, "ctas_per_sm must be >= 0");
+  if (c.tile_y + 2 * h->p.alpha > 256)
+    return fail(NRM_ERR_UNSUPPORTED, "tile_y + 2 alpha exceeds the TMA box limit");
+  const int out = h->p.out_dtype;
+  const unsigned ps = nrm::persistent_smem_bytes(c.tile_x, c.tile_y, h->p.alpha, c.stages);
+  const unsigned pl = nrm::plain_smem_bytes(c.tile_x, c.tile_y, h->p.alpha);
+  int rc = set_smem_attr(ks->persistent[out], ps);
+  if (rc) return rc;
+  rc = set_smem_attr(ks->plain[out], pl);
+  if (rc) return rc;
+  int occ = 0;
+  NRM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks->persistent[out], c.threads, ps),
+           "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (occ < 1) return fail(NRM_ERR_UNSUPPORTED, "persistent kernel does not fit on an SM");
+  const int per_sm = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, occ) : occ;
+  // Retire work that used the old graphs before replacing them.
+  rc = retire_all(h);
+  if (rc) return rc;
+  for (auto& s : h->slots) destroy_slot_graph(s);
+  h->cfg = c;
+  h->ks = ks;
+  h->persistent_grid = per_sm * h->sm_count;
+  return NRM_OK;
+}
+
+// (Re)builds a slot's graph: upload node -> [ev_start] -> kernel -> [ev_end].
+int build_slot_graph(nrm_handle* h, Slot& s) {
+  destroy_slot_graph(s);
+  NRM_CUDA(cudaGraphCreate(&s.graph, 0), "cudaGraphCreate");
+  NRM_CUDA(cudaGraphAddMemcpyNode1D(&s.copy_node, s.graph, nullptr, 0, s.dev, s.host,
+                                    nrm::block_bytes(s.capacity), cudaMemcpyHostToDevice),
+           "cudaGraphAddMemcpyNode1D");
+  cudaGraphNode_t prev = s.copy_node;
+  if (h->timing) {
+    cudaGraphNode_t e;
+    NRM_CUDA(cudaGraphAddEventRecordNode(&e, s.graph, &prev, 1, s.ev_start), "cudaGraphAddEventRecordNode");
+    prev = e;
+  }
+  nrm::BatchArgs args;
+  args.hdr = reinterpret_cast<const nrm::BatchHeader*>(s.dev);
+  args.tile_begin = reinterpret_cast<const int*>(static_cast<char*>(s.dev) + nrm::kTileBeginOffset);
+  args.frames = reinterpret_cast<const FrameDesc*>(static_cast<char*>(s.dev) + nrm::frames_offset(s.capacity));
+  args.stages = h->cfg.stages;
+  args.stage_bytes = nrm::stage_bytes_for(h->cfg.tile_x, h->cfg.tile_y, h->p.alpha);
+  nrm::Globals g = make_globals(h);
+  void* kargs[2] = {&args, &g};
+  cudaKernelNodeParams kp;
+  std::memset(&kp, 0, sizeof(kp));
+  kp.func = const_cast<void*>(h->ks->persistent[h->p.out_dtype]);
+  kp.gridDim = dim3(h->persistent_grid);
+  kp.blockDim = dim3(h->cfg.threads);
+  kp.sharedMemBytes = nrm::persistent_smem_bytes(h->cfg.tile_x, h->cfg.tile_y, h->p.alpha, h->cfg.stages);
+  kp.kernelParams = kargs;
+  cudaGraphNode_t kn;
+  NRM_CUDA(cudaGraphAddKernelNode(&kn, s.graph, &prev, 1, &kp), "cudaGraphAddKernelNode");
+  if (h->timing) {
+    cudaGraphNode_t e;
+    NRM_CUDA(cudaGraphAddEventRecordNode(&e, s.graph, &kn, 1, s.ev_end), "cudaGraphAddEventRecordNode");
+  }
+  NRM_CUDA(cudaGraphInstantiate(&s.exec, s.graph, 0), "cudaGraphInstantiate");
+  s.graph_timed = h->timing;
+  return NRM_OK;
+}
+
+int ensure_slot_capacity(nrm_handle* h, Slot& s, int n) {
+  if (s.capacity >= n && s.host && s.dev) return NRM_OK;
+  int cap = std::max(64, s.capacity);
+  while (cap < n) cap *= 2;
+  destroy_slot_graph(s);
+  if (s.host) cudaFreeHost(s.host);
+  if (s.dev) cudaFree(s.dev);
+  s.host = s.dev = nullptr;
+  s.capacity = 0;
+  const size_t bytes = nrm::block_bytes(cap);
+  NRM_CUDA(cudaHostAlloc(&s.host, bytes, cudaHostAllocDefault), "cudaHostAlloc");
+  NRM_CUDA(cudaMalloc(&s.dev, bytes), "cudaMalloc");
+  std::memset(s.host, 0, bytes);
+  s.capacity = cap;
+  (void)h;
+  return NRM_OK;
+}
+
+int validate_frame(const nrm_frame& f, int i, int out_dtype) {
+  if (f.H < 0 || f.W < 0) return fail(NRM_ERR_INVALID_ARG, "frame %d: negative size", i);
+  if ((long long)f.H * f.W == 0) return NRM_OK;
+  if (!f.depth || !f.normals || !f.valid) return fail(NRM_ERR_INVALID_ARG, "frame %d: NULL buffer", i);
+  if (f.depth_pitch < f.W || f.out_pitch < f.W) return fail(NRM_ERR_INVALID_ARG, "frame %d: pitch < W", i);
+  if (f.in_dtype != NRM_IN_F32_M && f.in_dtype != NRM_IN_U16_MM)
+    return fail(NRM_ERR_INVALID_ARG, "frame %d: in_dtype %d", i, f.in_dtype);
+  const uintptr_t na = out_dtype == NRM_OUT_F32X4 ? 16 : 8;
+  if ((uintptr_t)f.normals % na) return fail(NRM_ERR_INVALID_ARG, "frame %d: normals not %d-byte aligned", i, (int)na);
+  const int eb = f.in_dtype == NRM_IN_U16_MM ? 2 : 4;
+  if ((uintptr_t)f.depth % eb) return fail(NRM_ERR_INVALID_ARG, "frame %d: depth not %d-byte aligned", i, eb);
+  if (f.H > (1 << 24) || f.W > (1 << 24)) return fail(NRM_ERR_UNSUPPORTED, "frame %d: dimension above 2^24", i);
+  return validate_intrinsics(f.K) ? fail(NRM_ERR_INVALID_ARG, "frame %d: bad intrinsics", i) : NRM_OK;
+}
+
+// ------------------------------------------------------------- JSON cache
+
+std::map<std::string, std::string> read_cache(const char* path) {
+  std::map<std::string, std::string> m;
+  std::ifstream in(path);
+  if (!in) return m;
+  std::stringstream ss;
+  ss << in.rdbuf();
+  std::string t = ss.str();
+  // Flat object: "key": [tx, ty, threads, stages, ctas], ...
+  size_t i = 0;
+  while (true) {
+    size_t k0 = t.find('"', i);
+    if (k0 == std::string::npos) break;
+    size_t k1 = t.find('"', k0 + 1);
+    if (k1 == std::string::npos) break;
+    size_t v0 = t.find('[', k1);
+    size_t v1 = t.find(']', v0 == std::string::npos ? k1 : v0);
+    if (v0 == std::string::npos || v1 == std::string::npos) break;
+    m[t.substr(k0 + 1, k1 - k0 - 1)] = t.substr(v0 + 1, v1 - v0 - 1);
+    i = v1 + 1;
+  }
+  return m;
+}
+
+void write_cache(const char* path, const std::map<std::string, std::string>& m) {
+  std::string tmp = std::string(path) + ".tmp";
+  std::ofstream out(tmp);
+  if (!out) return;
+  out << "{\n";
+  size_t n = 0;
+  for (const auto& kv : m) {
+    out << "  \"" << kv.first << "\": [" << kv.second << "]" << (++n < m.size() ? ",\n" : "\n");
+  }
+  out << "}\n";
+  out.close();
+  std::rename(tmp.c_str(), path);
+}
+
+std::string tune_key(const nrm_handle* h, const nrm_frame* f, int n) {
+  long long px = 0;
+  int maxw = 0, dtypes = 0;
+  for (int i = 0; i < n; ++i) {
+    px += (long long)f[i].H * f[i].W;
+    maxw = std::max(maxw, f[i].W);
+    dtypes |= 1 << f[i].in_dtype;
+  }
+  int lpx = 0;
+  while ((1LL << (lpx + 1)) <= px) ++lpx;
+  int lw = 0;
+  while ((1 << (lw + 1)) <= maxw) ++lw;
+  std::string name = h->gpu_name;
+  for (auto& ch : name)
+    if (ch == '"' || ch == '\\') ch = '_';
+  std::ostringstream k;
+  k << name << "|sm" << h->sm_count << "|in" << dtypes << "|out" << h->p.out_dtype << "|a" << h->p.alpha
+    << "|px2^" << lpx << "|w2^" << lw;
+  return k.str();
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+void nrm_default_params(nrm_params* p) {
+  if (!p) return;
+  p->alpha = 2;
+  p->mask_mode = NRM_MASK_SECANT;
+  p->tau = 12.0f;
+  p->depth_scale = 0.001f;
+  p->in_dtype = NRM_IN_F32_M;
+  p->out_dtype = NRM_OUT_F32X4;
+  p->orient_to_camera = 0;
+}
+
+const char* nrm_status_string(int status) {
+  switch (status) {
+    case NRM_OK: return "NRM_OK";
+    case NRM_ERR_INVALID_ARG: return "NRM_ERR_INVALID_ARG";
+    case NRM_ERR_UNSUPPORTED: return "NRM_ERR_UNSUPPORTED";
+    case NRM_ERR_CUDA: return "NRM_ERR_CUDA";
+    case NRM_ERR_OOM: return "NRM_ERR_OOM";
+    case NRM_ERR_TIMEOUT: return "NRM_ERR_TIMEOUT";
+    case NRM_ERR_NO_DEVICE: return "NRM_ERR_NO_DEVICE";
+    default: return "NRM_ERR_UNKNOWN";
+  }
+}
+
+const char* nrm_last_error(void) { return g_last_error.c_str(); }
+
+const char* nrm_version(void) { return "nrm 0.1 (sm_103a)"; }
+
+int nrm_create(const nrm_intrinsics* K, int H, int W, const nrm_params* p, nrm_handle** out) {
+  g_last_error.clear();
+  if (!out) return fail(NRM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  nrm_params params;
+  nrm_default_params(&params);
+  if (p) params = *p;
+  int rc = validate_params(params);
+  if (rc) return rc;
+  if (H < 0 || W < 0) return fail(NRM_ERR_INVALID_ARG, "negative size");
+  if ((H > 0) != (W > 0)) return fail(NRM_ERR_INVALID_ARG, "H and W must both be 0 or both positive");
+  if (H > 0) {
+    if (!K) return fail(NRM_ERR_INVALID_ARG, "K is NULL");
+    rc = validate_intrinsics(*K);
+    if (rc) return rc;
+    if (H > (1 << 24) || W > (1 << 24)) return fail(NRM_ERR_UNSUPPORTED, "dimension above 2^24");
+  }
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) return fail(NRM_ERR_NO_DEVICE, "no CUDA device visible");
+  nrm_handle* h = new nrm_handle();
+  h->p = params;
+  h->H = H;
+  h->W = W;
+  if (K) h->K = *K;
+  cudaGetDevice(&h->device);
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "cudaGetDeviceProperties");
+  }
+  if (prop.major < 10) {
+    delete h;
+    return fail(NRM_ERR_UNSUPPORTED, "device %s is sm_%d%d; this library is built for sm_103a", prop.name,
+                prop.major, prop.minor);
+  }
+  h->sm_count = prop.multiProcessorCount;
+  std::snprintf(h->gpu_name, sizeof(h->gpu_name), "%s", prop.name);
+  if ((e = cudaMalloc(&h->d_status, sizeof(int))) != cudaSuccess ||
+      (e = cudaMemset(h->d_status, 0, sizeof(int))) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&h->last_single, cudaEventDisableTiming)) != cudaSuccess) {
+    nrm_destroy(h);
+    return cuda_fail(e, "handle allocation");
+  }
+  for (auto& s : h->slots) {
+    if ((e = cudaEventCreate(&s.ev_start)) != cudaSuccess || (e = cudaEventCreate(&s.ev_end)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming)) != cudaSuccess) {
+      nrm_destroy(h);
+      return cuda_fail(e, "cudaEventCreate");
+    }
+  }
+  nrm_tile_config c = {128, 16, 256, 3, 0};
+  rc = configure(h, c);
+  if (rc) {
+    std::string msg = g_last_error;
+    nrm_destroy(h);
+    g_last_error = msg;
+    return rc;
+  }
+  *out = h;
+  return NRM_OK;
+}
+
+void nrm_destroy(nrm_handle* h) {
+  if (!h) return;
+  DeviceGuard guard(h->device);
+  for (auto& s : h->slots) {
+    if (s.in_flight && s.done) cudaEventSynchronize(s.done);
+    destroy_slot_graph(s);
+    if (s.host) cudaFreeHost(s.host);
+    if (s.dev) cudaFree(s.dev);
+    if (s.ev_start) cudaEventDestroy(s.ev_start);
+    if (s.ev_end) cudaEventDestroy(s.ev_end);
+    if (s.done) cudaEventDestroy(s.done);
+  }
+  if (h->last_single) {
+    cudaEventSynchronize(h->last_single);
+    cudaEventDestroy(h->last_single);
+  }
+  if (h->d_status) cudaFree(h->d_status);
+  delete h;
+}
+
+int nrm_estimate(nrm_handle* h, const void* depth, void* normals, uint8_t* valid, void* cuda_stream) {
+  g_last_error.clear();
+  if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
+  if (h->H == 0 || h->W == 0) return fail(NRM_ERR_INVALID_ARG, "handle was created for batched calls only");
+  nrm_frame f;
+  f.depth = depth;
+  f.normals = normals;
+  f.valid = valid;
+  f.H = h->H;
+  f.W = h->W;
+  f.depth_pitch = h->W;
+  f.out_pitch = h->W;
+  f.K = h->K;
+  f.in_dtype = h->p.in_dtype;
+  int rc = validate_frame(f, 0, h->p.out_dtype);
+  if (rc) return rc;
+  DeviceGuard guard(h->device);
+  const int TX = h->cfg.tile_x, TY = h->cfg.tile_y;
+  const int eb = f.in_dtype == NRM_IN_U16_MM ? 2 : 4;
+  FrameDesc d;
+  make_desc(&d, depth, normals, valid, f.H, f.W, f.depth_pitch, f.out_pitch, f.K, f.in_dtype, h->p, TX, TY,
+            TX + 2 * nrm::pad_x(h->p.alpha, eb), TY + 2 * h->p.alpha);
+  nrm::Globals g = make_globals(h);
+  dim3 grid((f.W + TX - 1) / TX, (f.H + TY - 1) / TY);
+  if (grid.y > 65535) return fail(NRM_ERR_UNSUPPORTED, "too many tile rows for a plain launch");
+  void* args[2] = {&d, &g};
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  NRM_CUDA(cudaLaunchKernel(h->ks->plain[h->p.out_dtype], grid, dim3(h->cfg.threads), args,
+                            nrm::plain_smem_bytes(TX, TY, h->p.alpha), st),
+           "launch fwd_plain_kernel");
+  NRM_CUDA(cudaEventRecord(h->last_single, st), "cudaEventRecord");
+  return NRM_OK;
+}
+
+int nrm_estimate_batched(nrm_handle* h, const nrm_frame* frames, int n, void* cuda_stream) {
+  g_last_error.clear();
+  if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 0) return fail(NRM_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return NRM_OK;
+  if (!frames) return fail(NRM_ERR_INVALID_ARG, "frames is NULL");
+  const int TX = h->cfg.tile_x, TY = h->cfg.tile_y;
+  long long total = 0;
+  for (int i = 0; i < n; ++i) {
+    int rc = validate_frame(frames[i], i, h->p.out_dtype);
+    if (rc) return rc;
+    const long long tx = (frames[i].W + TX - 1) / TX, ty = (frames[i].H + TY - 1) / TY;
+    total += tx * ty;
+    if (total >= (1LL << 31) - 1) return fail(NRM_ERR_UNSUPPORTED, "batch exceeds 2^31 tiles");
+  }
+  if (total == 0) return NRM_OK;
+  DeviceGuard guard(h->device);
+  Slot& s = h->slots[h->next_slot];
+  h->next_slot = (h->next_slot + 1) % kSlots;
+  int rc = retire_slot(h, s);
+  if (rc) return rc;
+  rc = ensure_slot_capacity(h, s, n);
+  if (rc) return rc;
+  // Fill the pinned staging block.
+  char* base = static_cast<char*>(s.host);
+  nrm::BatchHeader* hdr = reinterpret_cast<nrm::BatchHeader*>(base);
+  int* tb = reinterpret_cast<int*>(base + nrm::kTileBeginOffset);
+  FrameDesc* fd = reinterpret_cast<FrameDesc*>(base + nrm::frames_offset(s.capacity));
+  int acc = 0;
+  for (int i = 0; i < n; ++i) {
+    const nrm_frame& f = frames[i];
+    const int eb = f.in_dtype == NRM_IN_U16_MM ? 2 : 4;
+    make_desc(&fd[i], f.depth, f.normals, f.valid, f.H, f.W, f.depth_pitch, f.out_pitch, f.K, f.in_dtype, h->p,
+              TX, TY, TX + 2 * nrm::pad_x(h->p.alpha, eb), TY + 2 * h->p.alpha);
+    fd[i].tile_begin = acc;
+    tb[i] = acc;
+    acc += fd[i].tiles_x * ((f.H + TY - 1) / TY);
+  }
+  tb[n] = acc;
+  hdr->n_frames = n;
+  hdr->total_tiles = acc;
+  if (!s.exec || s.graph_timed != h->timing) {
+    rc = build_slot_graph(h, s);
+    if (rc) return rc;
+  }
+  // Upload only the used part: header + tile_begin, and the used descriptors.
+  const size_t used = nrm::frames_offset(s.capacity) + sizeof(FrameDesc) * (size_t)n;
+  NRM_CUDA(cudaGraphExecMemcpyNodeSetParams1D(s.exec, s.copy_node, s.dev, s.host, used, cudaMemcpyHostToDevice),
+           "cudaGraphExecMemcpyNodeSetParams1D");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  NRM_CUDA(cudaGraphLaunch(s.exec, st), "cudaGraphLaunch");
+  NRM_CUDA(cudaEventRecord(s.done, st), "cudaEventRecord");
+  s.in_flight = true;
+  s.timed_launch = s.graph_timed;
+  s.tiles = acc;
+  return NRM_OK;
+}
+
+int nrm_backward(nrm_handle* h, const void* depth, const float* grad_normals, const uint8_t* valid,
+                 float* grad_depth, void* cuda_stream) {
+  g_last_error.clear();
+  if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
+  if (h->H == 0 || h->W == 0) return fail(NRM_ERR_INVALID_ARG, "handle was created for batched calls only");
+  if (h->p.in_dtype != NRM_IN_F32_M) return fail(NRM_ERR_UNSUPPORTED, "backward needs float32 depth");
+  if (!depth || !grad_normals || !valid || !grad_depth) return fail(NRM_ERR_INVALID_ARG, "NULL buffer");
+  if ((uintptr_t)grad_normals % 16) return fail(NRM_ERR_INVALID_ARG, "grad_normals not 16-byte aligned");
+  if ((uintptr_t)depth % 4 || (uintptr_t)grad_depth % 4) return fail(NRM_ERR_INVALID_ARG, "depth not 4-byte aligned");
+  DeviceGuard guard(h->device);
+  FrameDesc d;
+  const int p2 = nrm::pad_x(2 * h->p.alpha, 4);
+  make_desc(&d, depth, nullptr, const_cast<uint8_t*>(valid), h->H, h->W, h->W, h->W, h->K, NRM_IN_F32_M, h->p,
+            nrm::kBwdTileX, nrm::kBwdTileY, nrm::kBwdTileX + 2 * p2, nrm::kBwdTileY + 4 * h->p.alpha);
+  if ((h->H + nrm::kBwdTileY - 1) / nrm::kBwdTileY > 65535)
+    return fail(NRM_ERR_UNSUPPORTED, "too many tile rows for the backward launch");
+  nrm::Globals g = make_globals(h);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  NRM_CUDA(nrm::launch_backward(d, grad_normals, grad_depth, g, st), "launch bwd_kernel");
+  NRM_CUDA(cudaEventRecord(h->last_single, st), "cudaEventRecord");
+  return NRM_OK;
+}
+
+int nrm_sync_status(nrm_handle* h) {
+  if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
+  DeviceGuard guard(h->device);
+  int rc = retire_all(h);
+  if (rc) return rc;
+  int st = 0;
+  NRM_CUDA(cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy status");
+  NRM_CUDA(cudaMemset(h->d_status, 0, sizeof(int)), "cudaMemset status");
+  if (st != NRM_OK) return fail(st, "device reported %s", nrm_status_string(st));
+  return NRM_OK;
+}
+
+int nrm_get_config(const nrm_handle* h, nrm_tile_config* cfg) {
+  if (!h || !cfg) return fail(NRM_ERR_INVALID_ARG, "NULL argument");
+  *cfg = h->cfg;
+  return NRM_OK;
+}
+
+int nrm_set_config(nrm_handle* h, const nrm_tile_config* cfg) {
+  if (!h || !cfg) return fail(NRM_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard guard(h->device);
+  return configure(h, *cfg);
+}
+
+int nrm_enable_timing(nrm_handle* h, int enable) {
+  if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
+  h->timing = enable != 0;
+  return NRM_OK;
+}
+
+int nrm_get_stats(nrm_handle* h, nrm_stats* out) {
+  if (!h || !out) return fail(NRM_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard guard(h->device);
+  int rc = retire_all(h);
+  if (rc) return rc;
+  *out = h->stats;
+  return NRM_OK;
+}
+
+int nrm_reset_stats(nrm_handle* h) {
+  if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
+  DeviceGuard guard(h->device);
+  int rc = retire_all(h);
+  if (rc) return rc;
+  h->stats = nrm_stats{0, 0.0, 0};
+  return NRM_OK;
+}
+
+int nrm_autotune(nrm_handle* h, const nrm_frame* frames, int n, void* cuda_stream, const char* cache_path) {
+  g_last_error.clear();
+  if (!h || (!frames && n > 0) || n < 0) return fail(NRM_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return NRM_OK;
+  DeviceGuard guard(h->device);
+  const std::string key = tune_key(h, frames, n);
+  std::map<std::string, std::string> cache;
+  if (cache_path) {
+    cache = read_cache(cache_path);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      nrm_tile_config c;
+      if (std::sscanf(it->second.c_str(), "%d , %d , %d , %d , %d", &c.tile_x, &c.tile_y, &c.threads, &c.stages,
+                      &c.ctas_per_sm) == 5 &&
+          configure(h, c) == NRM_OK)
+        return NRM_OK;
+    }
+  }
+  const bool timing_was = h->timing;
+  h->timing = false;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaEvent_t e0, e1;
+  NRM_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+  NRM_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+  const nrm_tile_config start = h->cfg;
+  nrm_tile_config best = start;
+  float best_ms = INFINITY;
+  int rc = NRM_OK;
+  for (int i = 0; i < nrm::fwd_kernel_count() && rc == NRM_OK; ++i) {
+    const FwdKernelSet* k = nrm::fwd_kernel(i);
+    for (int stages = 2; stages <= 4; ++stages) {
+      nrm_tile_config c = {k->tile_x, k->tile_y, k->threads, stages, 0};
+      if (configure(h, c) != NRM_OK) continue;  // e.g. does not fit
+      for (int w = 0; w < 2 && rc == NRM_OK; ++w) rc = nrm_estimate_batched(h, frames, n, cuda_stream);
+      if (rc) break;
+      const int reps = 5;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && rc == NRM_OK; ++r) rc = nrm_estimate_batched(h, frames, n, cuda_stream);
+      cudaEventRecord(e1, st);
+      if (rc) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = fail(NRM_ERR_CUDA, "autotune: launch failed");
+        break;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->timing = timing_was;
+  int rc2 = configure(h, rc == NRM_OK ? best : start);
+  if (rc) return rc;
+  if (rc2) return rc2;
+  if (cache_path) {
+    char buf[128];
+    std::snprintf(buf, sizeof(buf), "%d, %d, %d, %d, %d", best.tile_x, best.tile_y, best.threads, best.stages,
+                  best.ctas_per_sm);
+    cache[key] = buf;
+    write_cache(cache_path, cache);
+  }
+  return NRM_OK;
+}
+
+}  // extern "C"

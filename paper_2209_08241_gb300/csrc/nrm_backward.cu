@@ -1,0 +1,153 @@
+// Adjoint of the forward normal map with respect to float32 depth, mask held
+// fixed (arXiv 2209.08241: derivatives of Eq. 4-6 and of the normalisation).
+//
+// For a valid pixel p with unit normal n_hat = s n / ||n|| (s = +-1) and upstream
+// gradient g_p = dL/d(n_hat_p):
+//   h_p = s (g_p - (g_p . n_hat) n_hat) / ||n||            (d n_hat / d n)^T g_p
+// and, with e_x = h_x - u1 h_z, e_y = h_y - v1 h_z (the n_z row of Eq. 6 folded in),
+// the four depth weights w_k(p) = h_p . dn/dd_k are
+//   w2 = -e_x a S35 - e_y b D35 + h_z c S35
+//   w4 = +e_x a S35 - e_y b D35 + h_z c S35
+//   w3 = -e_x a D24 - e_y b S24 + h_z c S24
+//   w5 = -e_x a D24 + e_y b S24 + h_z c S24
+// (a, b, c the Eq. 4-6 constants). dn/dd1 = 0. Each depth pixel q then gathers
+//   dL/dd_q = w2(q - alpha x) + w4(q + alpha x) + w3(q - alpha y) + w5(q + alpha y),
+// a deterministic gather with no atomics.
+//
+// One CTA per 64 x 16 output tile: a TMA load stages the depth halo of radius
+// 2 alpha; phase 1 computes (w2, w3, w4, w5) for the tile extended by alpha into
+// shared memory; phase 2 gathers.
+#include "nrm_device.cuh"
+
+namespace nrm {
+
+using namespace dev;
+
+namespace {
+
+constexpr int TX = kBwdTileX;
+constexpr int TY = kBwdTileY;
+constexpr int NT = kBwdThreads;
+
+__host__ __device__ inline unsigned depth_tile_bytes(int alpha) {
+  const int p2 = pad_x(2 * alpha, 4);
+  const unsigned b = (unsigned)((TX + 2 * p2) * (TY + 4 * alpha) * 4);
+  return (b + 127) / 128 * 128;
+}
+
+__host__ __device__ inline unsigned weight_tile_bytes(int alpha) {
+  return (unsigned)((TX + 2 * alpha) * (TY + 2 * alpha) * 16);
+}
+
+__global__ void __launch_bounds__(NT)
+    bwd_kernel(const __grid_constant__ FrameDesc fd, const float4* __restrict__ gn,
+               float* __restrict__ grad, const Globals g) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int alpha = g.alpha;
+  const int p2 = pad_x(2 * alpha, 4);
+  const int bw = TX + 2 * p2;      // depth tile pitch
+  const int bh = TY + 4 * alpha;
+  const int ex_w = TX + 2 * alpha;  // weight tile pitch
+  const int ex_h = TY + 2 * alpha;
+  float* dep = reinterpret_cast<float*>(smem);
+  float4* wts = reinterpret_cast<float4*>(smem + depth_tile_bytes(alpha));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + depth_tile_bytes(alpha) + weight_tile_bytes(alpha));
+  const int gx0 = blockIdx.x * TX;
+  const int gy0 = blockIdx.y * TY;
+  const int H = fd.H, W = fd.W;
+
+  if (fd.use_tma) {
+    const uint32_t b = smem_u32(bar);
+    if (threadIdx.x == 0) {
+      mbar_init(b, 1);
+      fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mbar_arrive_expect_tx(b, (uint32_t)(bw * bh * 4));
+      tma_load_2d(smem_u32(dep), &fd.tmap, gx0 - p2, gy0 - 2 * alpha, b);
+    }
+    const bool ok = mbar_wait_bounded(b, 0, g.timeout_ns);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        record_error(g.status, NRM_ERR_TIMEOUT);
+        mbar_wait_bounded(b, 0, g.timeout_ns);
+      }
+      return;
+    }
+  } else {
+    load_tile_plain(dep, bw, bh, fd, gx0 - p2, gy0 - 2 * alpha);
+    __syncthreads();
+  }
+
+  const FrameConsts k = {fd.a, fd.b, fd.c, fd.inv_fx, fd.inv_fy, fd.cx, fd.cy};
+  // Phase 1: weights of every pixel p of the extended tile.
+  for (int i = threadIdx.x; i < ex_w * ex_h; i += NT) {
+    const int ey = i / ex_w, ex = i - ey * ex_w;
+    const int px = gx0 - alpha + ex, py = gy0 - alpha + ey;
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (px >= 0 && py >= 0 && px < W && py < H) {
+      const long long o = (long long)py * fd.out_pitch + px;
+      if (__ldg(fd.valid + o)) {
+        // p's centre in the depth tile: (px - (gx0 - p2), py - (gy0 - 2 alpha)).
+        const StencilSums s = stencil_sums(dep + (ey + alpha) * bw + (ex - alpha + p2), alpha, bw);
+        if (s.ok) {
+          const float u1 = ((float)px - k.cx) * k.inv_fx;
+          const float v1 = ((float)py - k.cy) * k.inv_fy;
+          float nx, ny, nz, P;
+          closed_form_normal(s, k, u1, v1, nx, ny, nz, P);
+          const float q = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+          const float inv = rsqrtf(q);
+          const float hx0 = nx * inv, hy0 = ny * inv, hz0 = nz * inv;
+          const float4 gv = __ldg(gn + o);
+          const float gd = fmaf(gv.x, hx0, fmaf(gv.y, hy0, gv.z * hz0));
+          const float si = g.sign * inv;
+          const float hx = (gv.x - gd * hx0) * si;
+          const float hy = (gv.y - gd * hy0) * si;
+          const float hz = (gv.z - gd * hz0) * si;
+          const float ex_ = fmaf(-u1, hz, hx);
+          const float ey_ = fmaf(-v1, hz, hy);
+          const float ea = ex_ * k.a, eb = ey_ * k.b, hc = hz * k.c;
+          w.x = -ea * s.S35 - eb * s.D35 + hc * s.S35;  // w2
+          w.y = -ea * s.D24 - eb * s.S24 + hc * s.S24;  // w3
+          w.z = ea * s.S35 - eb * s.D35 + hc * s.S35;   // w4
+          w.w = -ea * s.D24 + eb * s.S24 + hc * s.S24;  // w5
+        }
+      }
+    }
+    wts[i] = w;
+  }
+  __syncthreads();
+  // Phase 2: gather.
+  for (int i = threadIdx.x; i < TX * TY; i += NT) {
+    const int ly = i / TX, lx = i - ly * TX;
+    const int qx = gx0 + lx, qy = gy0 + ly;
+    if (qx >= W || qy >= H) continue;
+    const int c = (ly + alpha) * ex_w + (lx + alpha);
+    const float v = wts[c - alpha].x + wts[c + alpha].z + wts[c - alpha * ex_w].y +
+                    wts[c + alpha * ex_w].w;
+    grad[(long long)qy * fd.depth_pitch + qx] = v;
+  }
+}
+
+}  // namespace
+
+unsigned bwd_smem_bytes(int alpha) {
+  return depth_tile_bytes(alpha) + weight_tile_bytes(alpha) + 16;
+}
+
+cudaError_t launch_backward(const FrameDesc& fd, const float* grad_normals, float* grad_depth,
+                            const Globals& g, cudaStream_t stream) {
+  const unsigned smem = bwd_smem_bytes(g.alpha);
+  static int configured_bytes = 0;
+  if ((int)smem > configured_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured_bytes = (int)smem;
+  }
+  dim3 grid((fd.W + TX - 1) / TX, (fd.H + TY - 1) / TY);
+  bwd_kernel<<<grid, NT, smem, stream>>>(fd, reinterpret_cast<const float4*>(grad_normals), grad_depth, g);
+  return cudaGetLastError();
+}
+
+}  // namespace nrm

@@ -1,0 +1,191 @@
+// Forward kernels: fused single-pass normal estimation (arXiv 2209.08241,
+// Section 3.1 Eq. 4-6 and the Section 3.2 discontinuity mask) for sm_103a.
+//
+// Both kernels stage a halo tile of depth, (TX + 2 pad) x (TY + 2 alpha), into
+// shared memory with one 2-D TMA load (cp.async.bulk.tensor, mbarrier
+// completion; the tensor map's out-of-bounds zero fill doubles as "invalid
+// depth" at the image border), then every thread evaluates its pixels from
+// shared memory and streams float4/half4 normals and packed mask bytes out.
+//
+//  fwd_plain_kernel       one CTA per tile of one frame (the per-frame launch);
+//  fwd_persistent_kernel  a persistent grid walks the (frame, tile) work list of
+//                         a whole batch with an S-stage TMA pipeline: while a
+//                         tile is computed, the next S-1 tiles are in flight.
+#include "nrm_device.cuh"
+
+namespace nrm {
+
+using namespace dev;
+
+template <int TX, int TY, int NT, bool HALF>
+__global__ void __launch_bounds__(NT)
+    fwd_plain_kernel(const __grid_constant__ FrameDesc fd, const Globals g) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int alpha = g.alpha;
+  const bool u16 = fd.in_dtype == NRM_IN_U16_MM;
+  const int eb = u16 ? 2 : 4;
+  const int padx = pad_x(alpha, eb);
+  const int bw = TX + 2 * padx;
+  const int bh = TY + 2 * alpha;
+  const int gx0 = blockIdx.x * TX;
+  const int gy0 = blockIdx.y * TY;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_bytes_for(TX, TY, alpha));
+
+  if (fd.use_tma) {
+    const uint32_t b = smem_u32(bar);
+    if (threadIdx.x == 0) {
+      mbar_init(b, 1);
+      fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mbar_arrive_expect_tx(b, (uint32_t)(bw * bh * eb));
+      tma_load_2d(smem_u32(smem), &fd.tmap, gx0 - padx, gy0 - alpha, b);
+    }
+    const bool ok = mbar_wait_bounded(b, 0, g.timeout_ns);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        record_error(g.status, NRM_ERR_TIMEOUT);
+        mbar_wait_bounded(b, 0, g.timeout_ns);  // let the copy land before exiting
+      }
+      return;
+    }
+  } else {
+    if (u16)
+      load_tile_plain(reinterpret_cast<uint16_t*>(smem), bw, bh, fd, gx0 - padx, gy0 - alpha);
+    else
+      load_tile_plain(reinterpret_cast<float*>(smem), bw, bh, fd, gx0 - padx, gy0 - alpha);
+    __syncthreads();
+  }
+  if (u16)
+    compute_tile<TX, TY, NT, HALF>(reinterpret_cast<const uint16_t*>(smem), bw, padx, fd, gx0, gy0, g);
+  else
+    compute_tile<TX, TY, NT, HALF>(reinterpret_cast<const float*>(smem), bw, padx, fd, gx0, gy0, g);
+}
+
+template <int TX, int TY, int NT, bool HALF>
+__global__ void __launch_bounds__(NT)
+    fwd_persistent_kernel(const BatchArgs args, const Globals g) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int S = args.stages;
+  const unsigned SB = args.stage_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * SB);
+  int4* info = reinterpret_cast<int4*>(smem + (size_t)S * SB + 128);
+  const int total = args.hdr->total_tiles;
+  const int nf = args.hdr->n_frames;
+  const int G = (int)gridDim.x;
+  const int my = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / G + 1 : 0;
+  if (my == 0) return;
+  const int alpha = g.alpha;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  // Producer state (thread 0 only): frame cursor over the work list (this
+  // CTA's tiles increase monotonically), last fenced tensor map, tiles issued.
+  int cur = 0;
+  int fenced = -1;
+  int issued = 0;
+  auto issue = [&](int j) {
+    const int t = (int)blockIdx.x + j * G;
+    while (cur + 1 < nf && __ldg(args.tile_begin + cur + 1) <= t) ++cur;
+    const FrameDesc* fd = args.frames + cur;
+    const int local = t - __ldg(args.tile_begin + cur);
+    const int tiles_x = fd->tiles_x;
+    const int ty = local / tiles_x;
+    const int tx = local - ty * tiles_x;
+    const int s = j % S;
+    const int tma = fd->use_tma;
+    info[s] = make_int4(cur, tx, ty, tma);
+    const uint32_t bar = smem_u32(&bars[s]);
+    if (tma) {
+      if (cur != fenced) {
+        fence_tensormap_acquire(&fd->tmap);
+        fenced = cur;
+      }
+      const int eb = fd->in_dtype == NRM_IN_U16_MM ? 2 : 4;
+      const int padx = pad_x(alpha, eb);
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(bar, (uint32_t)((TX + 2 * padx) * (TY + 2 * alpha) * eb));
+      tma_load_2d(smem_u32(smem + (size_t)s * SB), &fd->tmap, tx * TX - padx, ty * TY - alpha, bar);
+    } else {
+      mbar_arrive(bar);
+    }
+    ++issued;
+  };
+
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < S && j < my; ++j) issue(j);
+  }
+
+  for (int i = 0; i < my; ++i) {
+    const int s = i % S;
+    const bool ok = mbar_wait_bounded(smem_u32(&bars[s]), (uint32_t)((i / S) & 1), g.timeout_ns);
+    // The barrier also tells thread 0 that every thread has finished tile i-1.
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        record_error(g.status, NRM_ERR_TIMEOUT);
+        for (int j = i; j < issued; ++j)
+          mbar_wait_bounded(smem_u32(&bars[j % S]), (uint32_t)((j / S) & 1), g.timeout_ns);
+      }
+      return;
+    }
+    if (threadIdx.x == 0 && i >= 1 && i - 1 + S < my) issue(i - 1 + S);
+
+    const int4 si = info[s];
+    const FrameDesc& fd = args.frames[si.x];
+    const bool u16 = fd.in_dtype == NRM_IN_U16_MM;
+    const int padx = pad_x(alpha, u16 ? 2 : 4);
+    const int bw = TX + 2 * padx;
+    const int gx0 = si.y * TX;
+    const int gy0 = si.z * TY;
+    unsigned char* buf = smem + (size_t)s * SB;
+    if (!si.w) {
+      if (u16)
+        load_tile_plain(reinterpret_cast<uint16_t*>(buf), bw, TY + 2 * alpha, fd, gx0 - padx, gy0 - alpha);
+      else
+        load_tile_plain(reinterpret_cast<float*>(buf), bw, TY + 2 * alpha, fd, gx0 - padx, gy0 - alpha);
+      fence_proxy_async_smem();  // these generic writes precede later TMA writes here
+      __syncthreads();
+    }
+    if (u16)
+      compute_tile<TX, TY, NT, HALF>(reinterpret_cast<const uint16_t*>(buf), bw, padx, fd, gx0, gy0, g);
+    else
+      compute_tile<TX, TY, NT, HALF>(reinterpret_cast<const float*>(buf), bw, padx, fd, gx0, gy0, g);
+  }
+}
+
+#define NRM_FWD_SET(TX, TY, NT)                                                            \
+  {TX, TY, NT,                                                                             \
+   {(const void*)fwd_plain_kernel<TX, TY, NT, false>,                                      \
+    (const void*)fwd_plain_kernel<TX, TY, NT, true>},                                      \
+   {(const void*)fwd_persistent_kernel<TX, TY, NT, false>,                                 \
+    (const void*)fwd_persistent_kernel<TX, TY, NT, true>}}
+
+// The compiled tile configurations; the first is the default. TX is at most
+// 128 so that the halo box (TX + 2 pad <= 256 elements) fits one TMA box.
+static const FwdKernelSet kFwdSets[] = {
+    NRM_FWD_SET(128, 16, 256), NRM_FWD_SET(128, 8, 256),  NRM_FWD_SET(128, 32, 256),
+    NRM_FWD_SET(128, 8, 128),  NRM_FWD_SET(128, 16, 128), NRM_FWD_SET(128, 32, 512),
+    NRM_FWD_SET(128, 64, 512), NRM_FWD_SET(64, 16, 128),  NRM_FWD_SET(64, 32, 256),
+    NRM_FWD_SET(64, 64, 256),
+};
+
+int fwd_kernel_count() { return (int)(sizeof(kFwdSets) / sizeof(kFwdSets[0])); }
+
+const FwdKernelSet* fwd_kernel(int i) {
+  return (i >= 0 && i < fwd_kernel_count()) ? &kFwdSets[i] : nullptr;
+}
+
+const FwdKernelSet* fwd_kernel_find(int tile_x, int tile_y, int threads) {
+  for (int i = 0; i < fwd_kernel_count(); ++i) {
+    const FwdKernelSet& k = kFwdSets[i];
+    if (k.tile_x == tile_x && k.tile_y == tile_y && k.threads == threads) return &k;
+  }
+  return nullptr;
+}
+
+}  // namespace nrm

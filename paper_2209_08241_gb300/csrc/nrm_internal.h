@@ -1,0 +1,119 @@
+// Internal declarations shared by the library's translation units (kernels and
+// host C ABI). Not part of the public interface (include/nrm.h).
+#pragma once
+
+#include <cuda.h>  // CUtensorMap (type only; the driver entry point is looked up at run time)
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nrm.h"
+
+#if defined(__CUDACC__)
+#define NRM_HD __host__ __device__
+#else
+#define NRM_HD
+#endif
+
+namespace nrm {
+
+// Pixels along x of the halo pad: the TMA box must start on a 16-byte
+// boundary, so the left pad alpha is rounded up to 16 bytes of elements.
+NRM_HD inline int pad_x(int alpha, int elem_bytes) {
+  int q = 16 / elem_bytes;
+  return (alpha + q - 1) / q * q;
+}
+
+// One frame of a launch. 256 bytes; the tensor map must be 128-byte aligned.
+struct alignas(128) FrameDesc {
+  CUtensorMap tmap;        // 2-D map of the depth image, box (TX + 2 pad) x (TY + 2 alpha)
+  const void* depth;
+  void* normals;
+  uint8_t* valid;
+  long long depth_pitch;   // elements
+  long long out_pitch;     // pixels (normals and mask)
+  int H, W;
+  int tiles_x;
+  int tile_begin;          // first work-list index of this frame
+  // Eq. 4-6 constants with the depth unit folded in (u16: times depth_scale^2):
+  float a;                 // alpha / (4 fy)
+  float b;                 // alpha / (4 fx)
+  float c;                 // alpha^2 / (4 fx fy)
+  float inv_fx, inv_fy, cx, cy;
+  int in_dtype;            // NRM_IN_F32_M or NRM_IN_U16_MM
+  int use_tma;             // 1: TMA tile loads; 0: plain loads (unaligned base or pitch)
+  int mask_align;          // bytes: largest power of two (<= 16) dividing mask base and pitch
+  int pad_[3];
+};
+static_assert(sizeof(FrameDesc) == 256, "FrameDesc layout");
+
+// Header of a batch's device descriptor block, followed by tile_begin[n+1]
+// (at kTileBeginOffset) and then the FrameDesc array (at frames_offset()).
+struct BatchHeader {
+  int n_frames;
+  int total_tiles;
+  int pad_[14];
+};
+static_assert(sizeof(BatchHeader) == 64, "BatchHeader layout");
+constexpr size_t kTileBeginOffset = 64;
+inline size_t frames_offset(int capacity) {
+  size_t b = kTileBeginOffset + sizeof(int) * (size_t)(capacity + 1);
+  return (b + 255) / 256 * 256;
+}
+inline size_t block_bytes(int capacity) { return frames_offset(capacity) + sizeof(FrameDesc) * (size_t)capacity; }
+
+// Launch-wide parameters (by value).
+struct Globals {
+  int alpha;
+  int mask_mode;
+  float tau2;              // tau^2 (may be +inf)
+  float sign;              // +1 paper orientation, -1 towards the camera
+  int* status;             // device status word (first error wins)
+  unsigned long long timeout_ns;  // bound of every device-side wait
+};
+
+struct BatchArgs {
+  const BatchHeader* hdr;
+  const int* tile_begin;
+  const FrameDesc* frames;
+  int stages;
+  unsigned stage_bytes;    // bytes per pipeline stage (multiple of 128)
+};
+
+// A compiled forward tile configuration.
+struct FwdKernelSet {
+  int tile_x, tile_y, threads;
+  const void* plain[2];       // [out_dtype] fwd_plain_kernel<...>
+  const void* persistent[2];  // [out_dtype] fwd_persistent_kernel<...>
+};
+
+// All compiled forward configurations (nrm_forward_*.cu).
+int fwd_kernel_count();
+const FwdKernelSet* fwd_kernel(int i);
+const FwdKernelSet* fwd_kernel_find(int tile_x, int tile_y, int threads);
+
+// Stage buffer bytes for a tile config and alpha (max over input dtypes).
+NRM_HD inline unsigned stage_bytes_for(int tile_x, int tile_y, int alpha) {
+  unsigned f32 = (unsigned)((tile_x + 2 * pad_x(alpha, 4)) * (tile_y + 2 * alpha) * 4);
+  unsigned u16 = (unsigned)((tile_x + 2 * pad_x(alpha, 2)) * (tile_y + 2 * alpha) * 2);
+  unsigned m = f32 > u16 ? f32 : u16;
+  return (m + 127) / 128 * 128;
+}
+// Dynamic shared memory of the plain kernel (one stage + barrier + info).
+inline unsigned plain_smem_bytes(int tile_x, int tile_y, int alpha) {
+  return stage_bytes_for(tile_x, tile_y, alpha) + 128;
+}
+// Dynamic shared memory of the persistent kernel.
+inline unsigned persistent_smem_bytes(int tile_x, int tile_y, int alpha, int stages) {
+  return stage_bytes_for(tile_x, tile_y, alpha) * stages + 128 + 16 * stages;
+}
+
+// Backward (adjoint) kernel for float32 depth: output tile and threads.
+constexpr int kBwdTileX = 64;
+constexpr int kBwdTileY = 16;
+constexpr int kBwdThreads = 256;
+unsigned bwd_smem_bytes(int alpha);
+// fd.tmap must map the depth with box (kBwdTileX + 2 pad_x(2 alpha, 4)) x (kBwdTileY + 4 alpha).
+cudaError_t launch_backward(const FrameDesc& fd, const float* grad_normals, float* grad_depth,
+                            const Globals& g, cudaStream_t stream);
+
+}  // namespace nrm

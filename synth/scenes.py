@@ -366,3 +366,15 @@ def unit_targets(n: int, H: int, W: int, seed: int = 4, device="cpu") -> torch.T
     t = torch.randn((n, H, W, 3), generator=g, dtype=torch.float64, device=torch.device(device))
     t = t / t.norm(dim=-1, keepdim=True)
     return t.to(torch.float32)
+
+
+def u16_batch(n: int = 64, W: int = 1920, H: int = 1080, seed0: int = 1000, device="cpu"):
+    """The full-HD uint16 batch: frame i uses seed seed0 + i. Returns [(depth, K)]."""
+    return [random_frame(seed0 + i, W, H, device, kind="u16") for i in range(n)]
+
+
+def mixed_batch(n: int = 256, seed: int = 3, device="cpu", kind="f32"):
+    """The uneven batch: n sizes drawn from SIZE_MIX; frame i uses seed 3000 + i.
+    Returns [(depth, K)]."""
+    return [random_frame(3000 + i, W, H, device, kind=kind)
+            for i, (W, H) in enumerate(size_mix(n, seed))]

@@ -1,0 +1,129 @@
+"""GPU adjoint parity: nrm_backward against the oracle's complex-step VJP on
+crops, against central finite differences of the GPU forward, and through the
+torch.autograd.Function, for the loss L = mean over valid pixels of
+(1 - n_hat . t) with random unit targets t (the differentiation workload:
+640 x 480 float32 depth without holes)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2209_08241_gb300 as nrm
+from synth import scenes
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+NT = max(1, min(16, os.cpu_count() or 1))
+
+
+def frame(seed=4, W=640, H=480):
+    return scenes.random_frame(4000 + seed, W, H, DEV, kind="f32", holes=False, clip_range=False)
+
+
+def loss_grad(n, m, t):
+    """dL/d(n_hat) of L = mean over valid of (1 - n_hat . t): -t / N_valid on valid."""
+    nv = m.sum().clamp(min=1).to(torch.float32)
+    g = torch.zeros_like(n)
+    g[..., :3] = -t * m[..., None].float() / nv
+    return g
+
+
+@pytest.mark.parametrize("alpha", [1, 2, 3])
+@pytest.mark.parametrize("orient", [False, True])
+def test_adjoint_matches_complex_step_oracle(alpha, orient):
+    d, K = frame(alpha)
+    H, W = d.shape
+    p = nrm.NormalParams(alpha=alpha, orient_to_camera=orient)
+    est = nrm.NormalEstimator(K, H, W, p)
+    n, m = est(d)
+    t = scenes.unit_targets(1, H, W, seed=4, device=DEV)[0]
+    g = loss_grad(n, m, t)
+    grad = est.backward(d, g, m)
+    est.sync_status()
+    dn = d.cpu().numpy()
+    gn = g[..., :3].double().cpu().numpy()
+    mv = m.cpu().numpy()
+    for (y0, x0) in ((0, 0), (200, 300), (H - 64, W - 64), (100, 17)):
+        ref = oracle.vjp(dn, K, gn, mv, alpha=alpha, orient=int(orient), crop=(y0, x0, 64, 64), nthreads=NT)
+        got = grad[y0:y0 + 64, x0:x0 + 64].double().cpu().numpy()
+        scale = np.abs(ref).max()
+        big = np.abs(ref) > 1e-3 * scale
+        rel = np.abs(got - ref)[big] / np.abs(ref)[big]
+        assert rel.max() <= 1e-3, (y0, x0, rel.max())
+        assert np.abs(got - ref)[~big].max(initial=0) <= 1e-3 * scale
+
+
+def test_adjoint_matches_central_differences_of_gpu_forward():
+    """64 random pixels with a stable mask; the FD step is the exact float32
+    difference of the perturbed depths (h = 1e-4 m requested)."""
+    d, K = frame(9)
+    H, W = d.shape
+    alpha = 2
+    est = nrm.NormalEstimator(K, H, W, nrm.NormalParams(alpha=alpha))
+    n, m = est(d)
+    t = scenes.unit_targets(1, H, W, seed=5, device=DEV)[0]
+    g = loss_grad(n, m, t)
+    grad = est.backward(d, g, m).cpu().numpy()
+    rng = np.random.default_rng(0)
+    checked = 0
+    gd = g[..., :3].double()
+    while checked < 64:
+        y = int(rng.integers(2 * alpha, H - 2 * alpha))
+        x = int(rng.integers(2 * alpha, W - 2 * alpha))
+        dp, dm = d.clone(), d.clone()
+        dp[y, x] += 1e-4
+        dm[y, x] -= 1e-4
+        h2 = float(dp[y, x].double() - dm[y, x].double())
+        n_p, m_p = est(dp)
+        n_m, m_m = est(dm)
+        if not (torch.equal(m_p, m) and torch.equal(m_m, m)):
+            continue
+        ys, xs = slice(y - alpha, y + alpha + 1), slice(x - alpha, x + alpha + 1)
+        Lp = float((n_p[ys, xs, :3].double() * gd[ys, xs]).sum())
+        Lm = float((n_m[ys, xs, :3].double() * gd[ys, xs]).sum())
+        fd = (Lp - Lm) / h2
+        a = grad[y, x]
+        assert abs(a - fd) <= 2e-2 * abs(fd) + 1e-9, (y, x, a, fd)
+        checked += 1
+
+
+def test_autograd_function_and_determinism():
+    d, K = frame(11)
+    H, W = d.shape
+    t = scenes.unit_targets(1, H, W, seed=6, device=DEV)[0]
+    x = d.clone().requires_grad_(True)
+    n, m = nrm.estimate_normals(x, K)
+    assert not m.requires_grad
+    valid = m.bool()
+    loss = (1.0 - (n[..., :3] * t).sum(-1))[valid].mean()
+    loss.backward()
+    est = nrm.NormalEstimator(K, H, W)
+    n2, m2 = est(d)
+    g = loss_grad(n2, m2, t)
+    direct = est.backward(d, g, m2)
+    direct2 = est.backward(d, g, m2)
+    assert torch.equal(direct, direct2)
+    torch.testing.assert_close(x.grad, direct, rtol=1e-5, atol=1e-6 * direct.abs().max().item())
+
+
+def test_backward_rejects_uint16_handles():
+    est = nrm.NormalEstimator((100.0, 100.0, 10.0, 10.0), 20, 20, in_dtype="u16")
+    d = torch.ones((20, 20), dtype=torch.uint16, device=DEV)
+    n, m = est(d)
+    with pytest.raises(nrm.NrmError):
+        est.backward(d, torch.zeros((20, 20, 4), device=DEV), m)
+
+
+def test_batch_of_32_losses():
+    """The differentiation workload: 32 frames of 640 x 480, forward + adjoint
+    per frame; gradients finite and zero outside the stencils of valid pixels."""
+    est = nrm.NormalEstimator(scenes.intrinsics_for(640, 480), 480, 640)
+    for i in range(32):
+        d, K = frame(100 + i)
+        n, m = est(d)
+        t = scenes.unit_targets(1, 480, 640, seed=100 + i, device=DEV)[0]
+        grad = est.backward(d, loss_grad(n, m, t), m)
+        assert torch.isfinite(grad).all()
+    est.sync_status()
