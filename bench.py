@@ -1,0 +1,479 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the boundary-aware normal estimator on GB300.
+
+Workload (one "step"): the batch of 64 full-HD (1920 x 1080) uint16 depth
+frames in millimetres (random-primitive scenes, Kinect-style noise, 1 mm
+quantisation, ~2 % dropout holes) through ONE batched persistent launch
+(replayed from the library's CUDA graph): unproject, four-direction averaging
+(Eq. 4-6), normalisation and the discontinuity mask fused in one pass; float4
+normals and a uint8 mask out. alpha = 2, secant statistic with tau = 12.
+
+Prints one JSON line. ``value`` is whole-job Mpixel/s with inputs resident in
+HBM; ``e2e`` is the same metric through the public API on pinned host buffers
+with the host<->device copies inside the timed region; ``roofline`` relates the
+kernel's algorithmic bytes (2 B depth + 16 B normal + 1 B mask per pixel) per
+launch to its mean duration, measured with CUDA events recorded inside the
+graph around the kernel node; ``cpu_baseline`` times the FP64 CPU oracle on a
+bounded sample of the same frames on this host's cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torchrun) every rank runs its own batch of 64 frames
+(frames are independent: weak scaling, no collective on the data path) and
+rank 0 reports the total pixels of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "normals Mpixel/s and % HBM roofline (batched vs per-frame, 1 GB300); p50/p99 latency"
+UNIT = "Mpixel/s"
+N_FRAMES, W_FULLHD, H_FULLHD = 64, 1920, 1080
+BYTES_PER_PX = 2 + 16 + 1       # uint16 depth in, float4 normal + uint8 mask out
+KERNEL_SOURCES = ("paper_2209_08241_gb300/csrc/nrm_forward.cu", "paper_2209_08241_gb300/csrc/nrm_device.cuh")
+
+# DRAM bytes per launch of the batched kernel from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum), valid only while the kernel sources hash to the key.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# --------------------------------------------------------------- distributed
+
+class Dist:
+    """Rank bookkeeping and the two reductions the benchmark needs."""
+
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, backend: str):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def reduce(self, value: float, op: str) -> float:
+        """max or sum over ranks (a scalar on the host; no data-path traffic)."""
+        if not self.pg:
+            return value
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([value], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX if op == "max" else self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# -------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of the SM clock and throttle reasons."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        self.t0 = time.time()
+
+    def stop(self):
+        if not self.proc:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        busy = [v for v in sm if mx and v >= 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- measurement
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def time_oracle_on(frames_np, K, cores, budget_s=12.0):
+    """Runs the FP64 oracle over whole frames (each with all cores), cycling
+    through the given frames, until the budget is spent (at least one frame,
+    at most 64). Returns (Mpx/s, frames, seconds)."""
+    import oracle
+    done_px, t0, nfr = 0, time.perf_counter(), 0
+    while nfr < 64:
+        d = frames_np[nfr % len(frames_np)]
+        oracle.forward(d, K, alpha=2, stat_mode=oracle.STAT_SECANT, tau=12.0, depth_scale=0.001,
+                       nthreads=cores)
+        done_px += d.size
+        nfr += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done_px / dt / 1e6, nfr, dt
+
+
+def bench_ours(args, dist: Dist):
+    import torch
+    N_FRAMES = args.frames
+
+    import paper_2209_08241_gb300 as nrm
+    from synth import scenes
+
+    torch.cuda.set_device(dist.local_rank)
+    dev = torch.device("cuda", dist.local_rank)
+    # This rank's batch: frames are independent, seeds differ per rank.
+    depth = torch.empty((N_FRAMES, H_FULLHD, W_FULLHD), dtype=torch.uint16, device=dev)
+    Ks = []
+    for i in range(N_FRAMES):
+        d, K = scenes.random_frame(1000 + N_FRAMES * dist.rank + i, W_FULLHD, H_FULLHD, dev, kind="u16")
+        depth[i].copy_(d)
+        Ks.append(K)
+    normals = torch.empty((N_FRAMES, H_FULLHD, W_FULLHD, 4), dtype=torch.float32, device=dev)
+    valid = torch.empty((N_FRAMES, H_FULLHD, W_FULLHD), dtype=torch.uint8, device=dev)
+    params = nrm.NormalParams(alpha=2, mask_mode="secant", tau=12.0, out_dtype="f32")
+    est = nrm.BatchedEstimator(params, device=dev)
+    frames, _ = est.make_frames([(depth[i], Ks[i]) for i in range(N_FRAMES)],
+                                [(normals[i], valid[i]) for i in range(N_FRAMES)])
+    px_per_step = N_FRAMES * H_FULLHD * W_FULLHD
+    stream = torch.cuda.current_stream(dev)
+
+    est.enable_timing(True)
+    clocks = ClockSampler(dist.local_rank)
+    clocks.start()
+    # Warm-up: at least W steps and at least one second of work (so that the
+    # clock sampler sees the GPU under load).
+    t_w = time.time()
+    w = 0
+    while w < args.warmup or time.time() - t_w < 1.0:
+        est.run(frames, N_FRAMES, stream)
+        w += 1
+        if w % 50 == 0:
+            torch.cuda.synchronize(dev)
+    torch.cuda.synchronize(dev)
+    est.reset_stats()
+    dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    e0.record(stream)
+    for _ in range(args.steps):
+        est.run(frames, N_FRAMES, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    torch.cuda.nvtx.range_pop()
+    dist.barrier()
+    clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st = est.stats()
+    est.sync_status()
+    kernel_ms = st["kernel_ms"] / max(1, st["launches"])
+
+    t_max = dist.reduce(ms, "max")
+    px_all = dist.reduce(float(px_per_step * args.steps), "sum")
+    value = px_all / (t_max / 1e3) / 1e6
+    ms_per_step = t_max / args.steps
+
+    peak, peak_kind = measured_peaks()
+    alg_bytes = px_per_step * BYTES_PER_PX
+    achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
+    khash = kernel_source_hash()
+    traffic = NCU_TRAFFIC.get(khash)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": f"{peak_kind} hbm_gbs", "kernel": "fwd_persistent_kernel<128,16,256,f32x4>",
+                "kernel_ms_mean": round(kernel_ms, 4), "algorithmic_bytes_per_launch": alg_bytes,
+                "kernel_source_hash": khash}
+
+    # End to end through the public API on pinned host buffers.
+    e2e = None
+    if not args.skip_e2e:
+        h_depth = depth.cpu().pin_memory()
+        h_normals = torch.empty(normals.shape, dtype=normals.dtype, pin_memory=True)
+        h_valid = torch.empty(valid.shape, dtype=valid.dtype, pin_memory=True)
+        est.enable_timing(False)
+        staging = est.run_host(h_depth, Ks, h_normals, h_valid)
+        torch.cuda.synchronize(dev)
+        n_e2e = max(3, min(args.steps, 20))
+        dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(n_e2e):
+            est.run_host(h_depth, Ks, h_normals, h_valid, staging=staging)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        dist.barrier()
+        e2e_ms = dist.reduce(e0.elapsed_time(e1), "max")
+        e2e_px = dist.reduce(float(px_per_step * n_e2e), "sum")
+        e2e = {"value": round(e2e_px / (e2e_ms / 1e3) / 1e6, 1), "unit": UNIT,
+               "h2d_bytes_per_step": int(h_depth.numel() * h_depth.element_size()),
+               "d2h_bytes_per_step": int(h_normals.numel() * h_normals.element_size()
+                                         + h_valid.numel() * h_valid.element_size()),
+               "steps": n_e2e}
+        del staging
+        est.enable_timing(True)
+
+    extra = {}
+    if not args.skip_extra:
+        extra = bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames, dev, stream,
+                             N_FRAMES)
+
+    cpu = None
+    if dist.rank == 0 and not args.skip_cpu:
+        cores = cpu_cores()
+        frames_np = [depth[i].cpu().numpy() for i in range(min(4, N_FRAMES))]
+        mpx, nfr, dt = time_oracle_on(frames_np, Ks[0], cores)
+        cpu = {"value": round(mpx, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{nfr} full-HD uint16 frames cycling over the first {len(frames_np)} of the batch "
+                         f"({nfr * H_FULLHD * W_FULLHD} px), "
+                         f"FP64 direct form, {cores} threads, {dt:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": dist.world,
+        "steps": args.steps, "warmup": w, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+        "data": "synthetic (seeded random-primitive scenes, Kinect-style noise, 1 mm quantisation, 2% holes)",
+        "config": {"workload": f"{N_FRAMES} x 1920x1080 uint16 depth (mm) -> float4 normals + uint8 mask, "
+                               "one batched persistent launch per step",
+                   "frames_per_gpu": N_FRAMES, "H": H_FULLHD, "W": W_FULLHD, "alpha": 2,
+                   "mask": "secant tau=12", "compute": "fp32", "out": "f32x4",
+                   "parallelism": f"frame-sharded x{dist.world} (no collective)",
+                   "l2": f"inputs larger than L2 ({px_per_step * BYTES_PER_PX / 1e6:.0f} MB moved per step)"},
+        "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+        "clocks": clocks.summary(), "gpu_launches": args.steps,
+        "extra": extra,
+    }
+    return line
+
+
+def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames, dev, stream, N_FRAMES):
+    """Secondary measurements: per-frame plain launches on the same batch, half
+    output, and the uneven-size batch (one persistent launch)."""
+    import torch
+    out = {}
+    reps = max(3, min(args.steps, 20))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    # Per-frame plain launches (one per frame) on the same 64 frames.
+    pf = nrm.NormalEstimator(Ks[0], H_FULLHD, W_FULLHD, est.params, in_dtype="u16", device=dev)
+    for _ in range(3):
+        for i in range(N_FRAMES):
+            pf.estimate(depth[i], normals[i], valid[i], stream)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        for i in range(N_FRAMES):
+            pf.estimate(depth[i], normals[i], valid[i], stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    px = N_FRAMES * H_FULLHD * W_FULLHD
+    out["per_frame_plain_mpx_s"] = round(px / (ms / 1e3) / 1e6, 1)
+    out["per_frame_plain_ms_per_step"] = round(ms, 4)
+    pf.sync_status()
+    del pf
+
+    # Half output on the same batch (11 B/px).
+    h16 = nrm.BatchedEstimator(nrm.NormalParams(out_dtype="f16"), device=dev)
+    n16 = torch.empty((N_FRAMES, H_FULLHD, W_FULLHD, 4), dtype=torch.float16, device=dev)
+    fr16, _ = h16.make_frames([(depth[i], Ks[i]) for i in range(N_FRAMES)],
+                              [(n16[i], valid[i]) for i in range(N_FRAMES)])
+    h16.enable_timing(True)
+    for _ in range(5):
+        h16.run(fr16, N_FRAMES, stream)
+    torch.cuda.synchronize(dev)
+    h16.reset_stats()
+    e0.record(stream)
+    for _ in range(reps):
+        h16.run(fr16, N_FRAMES, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    st = h16.stats()
+    kms = st["kernel_ms"] / max(1, st["launches"])
+    peak, _ = measured_peaks()
+    out["u16_half4_mpx_s"] = round(px / (ms / 1e3) / 1e6, 1)
+    out["u16_half4_hbm_frac"] = round(px * 11 / (kms / 1e3) / 1e9 / peak, 4)
+    h16.sync_status()
+    del h16, n16
+
+    # Uneven-size batch: 256 float32 frames from the size mix, one launch.
+    mix = scenes.mixed_batch(256, device=dev, kind="f32")
+    mpx = sum(d.numel() for d, _ in mix)
+    for od in ("f32", "f16"):
+        b = nrm.BatchedEstimator(nrm.NormalParams(out_dtype=od), device=dev)
+        outs = [(torch.empty((*d.shape, 4), dtype=torch.float32 if od == "f32" else torch.float16, device=dev),
+                 torch.empty(d.shape, dtype=torch.uint8, device=dev)) for d, _ in mix]
+        fr, _ = b.make_frames(mix, outs)
+        b.enable_timing(True)
+        for _ in range(3):
+            b.run(fr, len(mix), stream)
+        torch.cuda.synchronize(dev)
+        b.reset_stats()
+        e0.record(stream)
+        for _ in range(reps):
+            b.run(fr, len(mix), stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        st = b.stats()
+        kms = st["kernel_ms"] / max(1, st["launches"])
+        bpp = 4 + (16 if od == "f32" else 8) + 1
+        out[f"mixed256_f32in_{od}out_mpx_s"] = round(mpx / (ms / 1e3) / 1e6, 1)
+        out[f"mixed256_f32in_{od}out_hbm_frac"] = round(mpx * bpp / (kms / 1e3) / 1e9 / peak, 4)
+        b.sync_status()
+        del b, outs
+    out["mixed256_mpx"] = round(mpx / 1e6, 2)
+    del mix
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_reference(args, dist: Dist):
+    """The FP64 CPU oracle on this host's cores, on the same workload (frames of
+    the same full-HD uint16 batch), each step a bounded sample."""
+    import numpy as np
+    import torch
+
+    from synth import scenes
+
+    if dist.rank != 0:
+        return None
+    cores = cpu_cores()
+    import oracle
+    d, K = scenes.random_frame(1000, W_FULLHD, H_FULLHD, "cpu", kind="u16")
+    frame = d.numpy()
+    # Calibrate: rows per step so that (warm-up + steps) stays near 2.5 minutes.
+    t0 = time.perf_counter()
+    oracle.forward(frame, K, alpha=2, stat_mode=oracle.STAT_SECANT, tau=12.0, depth_scale=0.001,
+                   rows=(0, 108), nthreads=cores)
+    per_row = (time.perf_counter() - t0) / 108
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    rows = int(max(8, min(H_FULLHD, budget / max(per_row, 1e-9))))
+    for _ in range(args.warmup):
+        oracle.forward(frame, K, alpha=2, stat_mode=oracle.STAT_SECANT, tau=12.0, depth_scale=0.001,
+                       rows=(0, rows), nthreads=cores)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        r0 = (s * rows) % max(1, H_FULLHD - rows + 1)
+        oracle.forward(frame, K, alpha=2, stat_mode=oracle.STAT_SECANT, tau=12.0, depth_scale=0.001,
+                       rows=(r0, r0 + rows), nthreads=cores)
+    dt = time.perf_counter() - t0
+    px = rows * W_FULLHD * args.steps
+    value = px / dt / 1e6
+    sample = f"{rows} rows x {W_FULLHD} px of one full-HD uint16 frame per step, FP64 direct form, {cores} threads"
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
+        "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "64 x 1920x1080 uint16 depth (mm) -> normals + mask (bounded sample per step)",
+                   "alpha": 2, "mask": "secant tau=12"},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames", type=int, default=N_FRAMES,
+                    help="frames per GPU (default 64; smaller only for profiling)")
+    ap.add_argument("--skip-extra", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    dist = Dist()
+    if args.impl == "reference":
+        dist.init("gloo")
+        line = bench_reference(args, dist)
+    else:
+        dist.init("nccl")
+        line = bench_ours(args, dist)
+    if dist.rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
+if __name__ == "__main__":
+    main()

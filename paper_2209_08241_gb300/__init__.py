@@ -248,6 +248,34 @@ class BatchedEstimator(_Handle):
         self.run(arr, len(items), stream)
         return outs
 
+    def run_host(self, depth_host: torch.Tensor, Ks: Sequence, normals_host: torch.Tensor,
+                 valid_host: torch.Tensor, staging: dict | None = None, stream=None) -> dict:
+        """End-to-end call on HOST buffers for a stack of equal-size frames.
+
+        depth_host (n, H, W) float32/uint16, normals_host (n, H, W, 4) and
+        valid_host (n, H, W) uint8, all in pinned host memory. Copies the depth
+        to the device, runs one batched launch and copies normals and masks back,
+        all on one stream; returns the device staging buffers (reusable: pass
+        them back as ``staging``). The caller synchronises before reading."""
+        n, H, W = depth_host.shape
+        dev = self.device
+        if staging is None:
+            staging = {
+                "depth": torch.empty(depth_host.shape, dtype=depth_host.dtype, device=dev),
+                "normals": torch.empty(normals_host.shape, dtype=normals_host.dtype, device=dev),
+                "valid": torch.empty(valid_host.shape, dtype=torch.uint8, device=dev),
+            }
+            staging["frames"], _ = self.make_frames(
+                [(staging["depth"][i], Ks[i]) for i in range(n)],
+                [(staging["normals"][i], staging["valid"][i]) for i in range(n)])
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        with torch.cuda.stream(s):
+            staging["depth"].copy_(depth_host, non_blocking=True)
+            self.run(staging["frames"], n, s)
+            normals_host.copy_(staging["normals"], non_blocking=True)
+            valid_host.copy_(staging["valid"], non_blocking=True)
+        return staging
+
     def autotune(self, items: Sequence, outputs: Sequence | None = None, cache_path: str | None = None,
                  stream=None) -> dict:
         arr, _ = self.make_frames(items, outputs)

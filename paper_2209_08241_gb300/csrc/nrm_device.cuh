@@ -161,63 +161,174 @@ __device__ __forceinline__ uint32_t bits_to_bytes4(uint32_t b) {
 
 // --------------------------------------------------------- tile compute
 
-// Computes one TX x TY output tile from a shared-memory halo tile.
-//   sm:    tile origin = global (gx0 - padx, gy0 - alpha), row pitch bw elements
-//   Normals: float4 (HALF = false) or 4 x half (HALF = true) per pixel.
+// The frame fields the tile loop needs, read once per tile into registers.
+// The orientation sign is folded into the Eq. 4-6 constants: the normal is
+// linear in (a, b, c), so scaling them by -1 negates n and leaves q = n . n
+// and P^2 unchanged.
+struct TileFrame {
+  float a, b, c, inv_fx, inv_fy, cx, cy;
+  int H, W;
+  long long out_pitch;
+  void* normals;
+  uint8_t* valid;
+  int mask_align;
+};
+
+__device__ __forceinline__ TileFrame tile_frame(const FrameDesc& fd, float sign) {
+  TileFrame f;
+  f.a = -sign * fd.a;  // n_x = -a S35 D24  ->  (A S35) D24 with A = -sign a
+  f.b = -sign * fd.b;
+  f.c = sign * fd.c;
+  f.inv_fx = fd.inv_fx;
+  f.inv_fy = fd.inv_fy;
+  f.cx = fd.cx;
+  f.cy = fd.cy;
+  f.H = fd.H;
+  f.W = fd.W;
+  f.out_pitch = fd.out_pitch;
+  f.normals = fd.normals;
+  f.valid = fd.valid;
+  f.mask_align = fd.mask_align;
+  return f;
+}
+
+// Decodes one staged depth element to float; an invalid depth becomes NaN so
+// that every quantity computed from it is NaN and fails the mask comparison.
+// float32: valid iff 0 < d <= FLT_MAX, i.e. bits - 1 < 0x7F7FFFFF (unsigned).
+__device__ __forceinline__ float decode_depth(float d) {
+  return (__float_as_uint(d) - 1u) < 0x7F7FFFFFu ? d : __int_as_float(0x7fc00000);
+}
+// uint16: exact conversion (2^23 + u is representable; subtracting 2^23 is
+// exact); raw 0 is invalid. The depth scale is folded into a, b, c.
+__device__ __forceinline__ float decode_depth_u16(uint32_t u) {
+  const float f = __uint_as_float(0x4B000000u | u) - 8388608.0f;
+  return u != 0u ? f : __int_as_float(0x7fc00000);
+}
+
+// Staged tile (TMA box, native dtype) -> decoded float tile, n elements
+// (a multiple of 4; both buffers 16-byte aligned).
+template <int NT>
+__device__ __forceinline__ void decode_tile(const float* __restrict__ src, float* __restrict__ dst, int n) {
+  for (int i = threadIdx.x * 4; i < n; i += NT * 4) {
+    float4 v = *reinterpret_cast<const float4*>(src + i);
+    v.x = decode_depth(v.x);
+    v.y = decode_depth(v.y);
+    v.z = decode_depth(v.z);
+    v.w = decode_depth(v.w);
+    *reinterpret_cast<float4*>(dst + i) = v;
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ void decode_tile(const uint16_t* __restrict__ src, float* __restrict__ dst, int n) {
+  for (int i = threadIdx.x * 4; i < n; i += NT * 4) {
+    const uint2 r = *reinterpret_cast<const uint2*>(src + i);
+    float4 v;
+    v.x = decode_depth_u16(r.x & 0xFFFFu);
+    v.y = decode_depth_u16(r.x >> 16);
+    v.z = decode_depth_u16(r.y & 0xFFFFu);
+    v.w = decode_depth_u16(r.y >> 16);
+    *reinterpret_cast<float4*>(dst + i) = v;
+  }
+}
+
+// Plain-load path (frames whose base or pitch rules out TMA): reads the halo
+// box straight from global memory into the decoded float tile; outside the
+// image counts as invalid, exactly like the TMA zero fill.
+template <typename InT>
+__device__ __forceinline__ void load_tile_decoded(float* dst, int bw, int bh, const FrameDesc& fd, int x0,
+                                                  int y0) {
+  const InT* src = reinterpret_cast<const InT*>(fd.depth);
+  const int n = bw * bh;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int ly = i / bw, lx = i - ly * bw;
+    const int x = x0 + lx, y = y0 + ly;
+    float v = __int_as_float(0x7fc00000);
+    if (x >= 0 && y >= 0 && x < fd.W && y < fd.H) {
+      const InT raw = __ldg(src + (long long)y * fd.depth_pitch + x);
+      if constexpr (sizeof(InT) == 2)
+        v = decode_depth_u16(raw);
+      else
+        v = decode_depth(raw);
+    }
+    dst[i] = v;
+  }
+}
+
+// Computes one TX x TY output tile from the decoded float halo tile F
+// (origin global (gx0 - padx, gy0 - alpha), row pitch bw).
 // Warp w handles rows w, w + NW, ...; lane l handles columns 32 k + l, so each
 // store instruction of a warp covers 32 consecutive pixels (512 B of float4).
-// Mask bytes are gathered with one ballot per 32 pixels and written as
-// TX/32 consecutive bytes per lane.
-template <int TX, int TY, int NT, bool HALF, typename InT>
-__device__ __forceinline__ void compute_tile(const InT* __restrict__ sm, int bw, int padx,
-                                             const FrameDesc& fd, int gx0, int gy0,
-                                             const Globals& g) {
+// Per-column terms (u1, 1 + u1^2) are computed once per tile. Mask bytes are
+// gathered with one ballot per 32 pixels and written as TX/32 consecutive bytes
+// per lane.
+template <int TX, int TY, int NT, bool HALF, bool SECANT>
+__device__ __forceinline__ void compute_tile(const float* __restrict__ F, int bw, int padx,
+                                             const TileFrame& f, int gx0, int gy0, int alpha,
+                                             float tau2) {
   constexpr int NW = NT / 32;
   constexpr int CH = TX / 32;
   static_assert(TY % NW == 0, "rows must divide among warps");
   static_assert(CH == 2 || CH == 4, "TX must be 64 or 128");
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int alpha = g.alpha;
-  const int H = fd.H, W = fd.W;
-  const FrameConsts k = {fd.a, fd.b, fd.c, fd.inv_fx, fd.inv_fy, fd.cx, fd.cy};
-  const float sign = g.sign;
+
+  float u1[CH], ku[CH];
+  bool colok[CH];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int gx = gx0 + 32 * c + lane;
+    u1[c] = ((float)gx - f.cx) * f.inv_fx;
+    ku[c] = fmaf(u1[c], u1[c], 1.0f);
+    colok[c] = gx < f.W;
+  }
+  const int dv = alpha * bw;
 
 #pragma unroll 1
   for (int ly = warp; ly < TY; ly += NW) {
     const int gy = gy0 + ly;
-    if (gy >= H) break;
-    const float v1 = ((float)gy - k.cy) * k.inv_fy;
-    const InT* row = sm + (ly + alpha) * bw + padx;
+    if (gy >= f.H) break;
+    const float v1 = ((float)gy - f.cy) * f.inv_fy;
+    const float kv = v1 * v1;
+    const float* row = F + (ly + alpha) * bw + padx + lane;
+    const long long out_row = (long long)gy * f.out_pitch + gx0 + lane;
     uint32_t ballots[CH];
-    const long long out_row = (long long)gy * fd.out_pitch;
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
-      const int lx = 32 * c + lane;
-      const int gx = gx0 + lx;
-      const StencilSums s = stencil_sums(row + lx, alpha, bw);
-      const float u1 = ((float)gx - k.cx) * k.inv_fx;
-      float nx, ny, nz, P;
-      closed_form_normal(s, k, u1, v1, nx, ny, nz, P);
+      const float* p = row + 32 * c;
+      const float d1 = p[0];
+      const float d2 = p[alpha], d4 = p[-alpha];
+      const float d3 = p[dv], d5 = p[-dv];
+      // Eq. 4-6 (Section 3.1).
+      const float S24 = d2 + d4, D24 = d2 - d4;
+      const float S35 = d3 + d5, D35 = d3 - d5;
+      const float nx = (f.a * S35) * D24;
+      const float ny = (f.b * S24) * D35;
+      const float P = (f.c * S24) * S35;  // n . (u1, v1, 1) (times the sign)
+      const float nz = fmaf(-u1[c], nx, fmaf(-v1, ny, P));
       const float q = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
-      const float ray2 = fmaf(u1, u1, fmaf(v1, v1, 1.0f));
-      const bool keep = keep_pixel(s.ok && gx < W, q, P, ray2, g.mask_mode, g.tau2);
-      // Select, not multiply: n may be NaN or infinite next to invalid depths.
-      const float inv = sign * rsqrtf(q);
+      // Section 3.2 mask in squared form; NaN (invalid depth) fails every test.
+      bool keep = colok[c] && (d1 == d1) && (q > 0.0f);
+      if (SECANT)
+        keep = keep && (q * (ku[c] + kv) <= tau2 * (P * P));
+      else
+        keep = keep && (q <= tau2);
+      // Select, not multiply: n is NaN next to invalid depths.
+      const float inv = rsqrtf(q);
       const float ox = keep ? nx * inv : 0.0f;
       const float oy = keep ? ny * inv : 0.0f;
       const float oz = keep ? nz * inv : 0.0f;
       ballots[c] = __ballot_sync(0xffffffffu, keep);
-      if (gx < W) {
+      if (colok[c]) {
         if (HALF) {
           __half2 xy = __floats2half2_rn(ox, oy);
           __half2 zw = __floats2half2_rn(oz, 0.0f);
           uint2 v;
           v.x = *reinterpret_cast<uint32_t*>(&xy);
           v.y = *reinterpret_cast<uint32_t*>(&zw);
-          __stcs(reinterpret_cast<uint2*>(fd.normals) + out_row + gx, v);
+          __stcs(reinterpret_cast<uint2*>(f.normals) + out_row + 32 * c, v);
         } else {
-          __stcs(reinterpret_cast<float4*>(fd.normals) + out_row + gx, make_float4(ox, oy, oz, 0.0f));
+          __stcs(reinterpret_cast<float4*>(f.normals) + out_row + 32 * c, make_float4(ox, oy, oz, 0.0f));
         }
       }
     }
@@ -229,8 +340,8 @@ __device__ __forceinline__ void compute_tile(const InT* __restrict__ sm, int bw,
     for (int c = 0; c < CH; ++c) word = (c == cidx) ? ballots[c] : word;
     const uint32_t bits = (word >> (first & 31)) & ((1u << CH) - 1u);
     const int gx = gx0 + first;
-    uint8_t* mrow = fd.valid + out_row;
-    if (gx + CH <= W && fd.mask_align >= CH) {
+    uint8_t* mrow = f.valid + (long long)gy * f.out_pitch;
+    if (gx + CH <= f.W && f.mask_align >= CH) {
       if (CH == 2) {
         const uint32_t v = bits_to_bytes4(bits);
         __stcs(reinterpret_cast<unsigned short*>(mrow + gx), (unsigned short)v);
@@ -240,10 +351,20 @@ __device__ __forceinline__ void compute_tile(const InT* __restrict__ sm, int bw,
     } else {
 #pragma unroll
       for (int j = 0; j < CH; ++j) {
-        if (gx + j < W) mrow[gx + j] = (uint8_t)((bits >> j) & 1u);
+        if (gx + j < f.W) mrow[gx + j] = (uint8_t)((bits >> j) & 1u);
       }
     }
   }
+}
+
+// Both mask modes of compute_tile, chosen once per tile.
+template <int TX, int TY, int NT, bool HALF>
+__device__ __forceinline__ void compute_tile_any(const float* __restrict__ F, int bw, int padx,
+                                                 const TileFrame& f, int gx0, int gy0, const Globals& g) {
+  if (g.mask_mode == NRM_MASK_SECANT)
+    compute_tile<TX, TY, NT, HALF, true>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
+  else
+    compute_tile<TX, TY, NT, HALF, false>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
 }
 
 // Loads the halo tile with plain loads (frames whose base or pitch rules out

@@ -29,8 +29,11 @@ __global__ void __launch_bounds__(NT)
   const int bh = TY + 2 * alpha;
   const int gx0 = blockIdx.x * TX;
   const int gy0 = blockIdx.y * TY;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_bytes_for(TX, TY, alpha));
+  const unsigned SB = stage_bytes_for(TX, TY, alpha);
+  float* F = reinterpret_cast<float*>(smem + SB);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SB + ftile_bytes_for(TX, TY, alpha));
 
+  bool ok = true;
   if (fd.use_tma) {
     const uint32_t b = smem_u32(bar);
     if (threadIdx.x == 0) {
@@ -42,25 +45,27 @@ __global__ void __launch_bounds__(NT)
       mbar_arrive_expect_tx(b, (uint32_t)(bw * bh * eb));
       tma_load_2d(smem_u32(smem), &fd.tmap, gx0 - padx, gy0 - alpha, b);
     }
-    const bool ok = mbar_wait_bounded(b, 0, g.timeout_ns);
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) {
-        record_error(g.status, NRM_ERR_TIMEOUT);
-        mbar_wait_bounded(b, 0, g.timeout_ns);  // let the copy land before exiting
-      }
-      return;
+    ok = mbar_wait_bounded(b, 0, g.timeout_ns);
+    if (ok) {
+      if (u16)
+        decode_tile<NT>(reinterpret_cast<const uint16_t*>(smem), F, bw * bh);
+      else
+        decode_tile<NT>(reinterpret_cast<const float*>(smem), F, bw * bh);
     }
   } else {
     if (u16)
-      load_tile_plain(reinterpret_cast<uint16_t*>(smem), bw, bh, fd, gx0 - padx, gy0 - alpha);
+      load_tile_decoded<uint16_t>(F, bw, bh, fd, gx0 - padx, gy0 - alpha);
     else
-      load_tile_plain(reinterpret_cast<float*>(smem), bw, bh, fd, gx0 - padx, gy0 - alpha);
-    __syncthreads();
+      load_tile_decoded<float>(F, bw, bh, fd, gx0 - padx, gy0 - alpha);
   }
-  if (u16)
-    compute_tile<TX, TY, NT, HALF>(reinterpret_cast<const uint16_t*>(smem), bw, padx, fd, gx0, gy0, g);
-  else
-    compute_tile<TX, TY, NT, HALF>(reinterpret_cast<const float*>(smem), bw, padx, fd, gx0, gy0, g);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      record_error(g.status, NRM_ERR_TIMEOUT);
+      mbar_wait_bounded(smem_u32(bar), 0, g.timeout_ns);  // let the copy land before exiting
+    }
+    return;
+  }
+  compute_tile_any<TX, TY, NT, HALF>(F, bw, padx, tile_frame(fd, g.sign), gx0, gy0, g);
 }
 
 template <int TX, int TY, int NT, bool HALF>
@@ -69,14 +74,16 @@ __global__ void __launch_bounds__(NT)
   extern __shared__ __align__(128) unsigned char smem[];
   const int S = args.stages;
   const unsigned SB = args.stage_bytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * SB);
-  int4* info = reinterpret_cast<int4*>(smem + (size_t)S * SB + 128);
+  const int alpha = g.alpha;
+  const unsigned FB = ftile_bytes_for(TX, TY, alpha);
+  unsigned char* fbase = smem + (size_t)S * SB;  // two decoded tiles of FB bytes
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * SB + 2 * FB);
+  int4* info = reinterpret_cast<int4*>(smem + (size_t)S * SB + 2 * FB + 128);
   const int total = args.hdr->total_tiles;
   const int nf = args.hdr->n_frames;
   const int G = (int)gridDim.x;
   const int my = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / G + 1 : 0;
   if (my == 0) return;
-  const int alpha = g.alpha;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) mbar_init(smem_u32(&bars[s]), 1);
@@ -108,11 +115,10 @@ __global__ void __launch_bounds__(NT)
       }
       const int eb = fd->in_dtype == NRM_IN_U16_MM ? 2 : 4;
       const int padx = pad_x(alpha, eb);
-      fence_proxy_async_smem();
       mbar_arrive_expect_tx(bar, (uint32_t)((TX + 2 * padx) * (TY + 2 * alpha) * eb));
       tma_load_2d(smem_u32(smem + (size_t)s * SB), &fd->tmap, tx * TX - padx, ty * TY - alpha, bar);
     } else {
-      mbar_arrive(bar);
+      mbar_arrive(bar);  // plain-load tile: the consumers read global memory themselves
     }
     ++issued;
   };
@@ -124,7 +130,31 @@ __global__ void __launch_bounds__(NT)
   for (int i = 0; i < my; ++i) {
     const int s = i % S;
     const bool ok = mbar_wait_bounded(smem_u32(&bars[s]), (uint32_t)((i / S) & 1), g.timeout_ns);
-    // The barrier also tells thread 0 that every thread has finished tile i-1.
+    const int4 si = info[s];
+    const FrameDesc& fd = args.frames[si.x];
+    const bool u16 = fd.in_dtype == NRM_IN_U16_MM;
+    const int padx = pad_x(alpha, u16 ? 2 : 4);
+    const int bw = TX + 2 * padx;
+    const int bh = TY + 2 * alpha;
+    const int gx0 = si.y * TX;
+    const int gy0 = si.z * TY;
+    // Decoded tiles alternate between two buffers: the barrier below (one per
+    // tile) then also guarantees that tile i - 2's buffer is no longer read.
+    float* F = reinterpret_cast<float*>(fbase + (i & 1) * FB);
+    if (ok) {
+      if (si.w) {
+        const unsigned char* stage = smem + (size_t)s * SB;
+        if (u16)
+          decode_tile<NT>(reinterpret_cast<const uint16_t*>(stage), F, bw * bh);
+        else
+          decode_tile<NT>(reinterpret_cast<const float*>(stage), F, bw * bh);
+      } else {
+        if (u16)
+          load_tile_decoded<uint16_t>(F, bw, bh, fd, gx0 - padx, gy0 - alpha);
+        else
+          load_tile_decoded<float>(F, bw, bh, fd, gx0 - padx, gy0 - alpha);
+      }
+    }
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         record_error(g.status, NRM_ERR_TIMEOUT);
@@ -133,28 +163,9 @@ __global__ void __launch_bounds__(NT)
       }
       return;
     }
-    if (threadIdx.x == 0 && i >= 1 && i - 1 + S < my) issue(i - 1 + S);
-
-    const int4 si = info[s];
-    const FrameDesc& fd = args.frames[si.x];
-    const bool u16 = fd.in_dtype == NRM_IN_U16_MM;
-    const int padx = pad_x(alpha, u16 ? 2 : 4);
-    const int bw = TX + 2 * padx;
-    const int gx0 = si.y * TX;
-    const int gy0 = si.z * TY;
-    unsigned char* buf = smem + (size_t)s * SB;
-    if (!si.w) {
-      if (u16)
-        load_tile_plain(reinterpret_cast<uint16_t*>(buf), bw, TY + 2 * alpha, fd, gx0 - padx, gy0 - alpha);
-      else
-        load_tile_plain(reinterpret_cast<float*>(buf), bw, TY + 2 * alpha, fd, gx0 - padx, gy0 - alpha);
-      fence_proxy_async_smem();  // these generic writes precede later TMA writes here
-      __syncthreads();
-    }
-    if (u16)
-      compute_tile<TX, TY, NT, HALF>(reinterpret_cast<const uint16_t*>(buf), bw, padx, fd, gx0, gy0, g);
-    else
-      compute_tile<TX, TY, NT, HALF>(reinterpret_cast<const float*>(buf), bw, padx, fd, gx0, gy0, g);
+    // Stage s has been decoded by every thread: refill it with tile i + S.
+    if (threadIdx.x == 0 && i + S < my) issue(i + S);
+    compute_tile_any<TX, TY, NT, HALF>(F, bw, padx, tile_frame(fd, g.sign), gx0, gy0, g);
   }
 }
 

@@ -98,13 +98,22 @@ NRM_HD inline unsigned stage_bytes_for(int tile_x, int tile_y, int alpha) {
   unsigned m = f32 > u16 ? f32 : u16;
   return (m + 127) / 128 * 128;
 }
-// Dynamic shared memory of the plain kernel (one stage + barrier + info).
-inline unsigned plain_smem_bytes(int tile_x, int tile_y, int alpha) {
-  return stage_bytes_for(tile_x, tile_y, alpha) + 128;
+// Bytes of the decoded float halo tile (the larger uint16 pad; f32 frames use
+// a narrower pitch inside the same buffer).
+NRM_HD inline unsigned ftile_bytes_for(int tile_x, int tile_y, int alpha) {
+  unsigned b = (unsigned)((tile_x + 2 * pad_x(alpha, 2)) * (tile_y + 2 * alpha) * 4);
+  return (b + 127) / 128 * 128;
 }
-// Dynamic shared memory of the persistent kernel.
-inline unsigned persistent_smem_bytes(int tile_x, int tile_y, int alpha, int stages) {
-  return stage_bytes_for(tile_x, tile_y, alpha) * stages + 128 + 16 * stages;
+// Dynamic shared memory of the plain kernel: staging buffer, decoded tile,
+// barrier.
+NRM_HD inline unsigned plain_smem_bytes(int tile_x, int tile_y, int alpha) {
+  return stage_bytes_for(tile_x, tile_y, alpha) + ftile_bytes_for(tile_x, tile_y, alpha) + 128;
+}
+// Dynamic shared memory of the persistent kernel: `stages` staging buffers,
+// two decoded tiles, barriers and per-stage tile info.
+NRM_HD inline unsigned persistent_smem_bytes(int tile_x, int tile_y, int alpha, int stages) {
+  return stage_bytes_for(tile_x, tile_y, alpha) * stages + 2 * ftile_bytes_for(tile_x, tile_y, alpha) +
+         128 + 16 * stages;
 }
 
 // Backward (adjoint) kernel for float32 depth: output tile and threads.
