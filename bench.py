@@ -210,6 +210,15 @@ def bench_ours(args, dist: Dist):
                                 [(normals[i], valid[i]) for i in range(N_FRAMES)])
     px_per_step = N_FRAMES * H_FULLHD * W_FULLHD
     stream = torch.cuda.current_stream(dev)
+    if args.config:
+        tx, ty, nt, st = (int(v) for v in args.config.split(","))
+        est.set_config(tx, ty, nt, st)
+    elif not args.no_autotune:
+        # Tile shape, threads and pipeline depth for this workload (timed here;
+        # the library caches nothing between fresh processes without a path).
+        est.autotune([(depth[i], Ks[i]) for i in range(N_FRAMES)],
+                     [(normals[i], valid[i]) for i in range(N_FRAMES)])
+    tile = est.config()
 
     est.enable_timing(True)
     clocks = ClockSampler(dist.local_rank)
@@ -254,7 +263,7 @@ def bench_ours(args, dist: Dist):
     traffic = NCU_TRAFFIC.get(khash)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": f"{peak_kind} hbm_gbs", "kernel": "fwd_persistent_kernel<128,16,256,f32x4>",
+                "peak_source": f"{peak_kind} hbm_gbs", "kernel": f"fwd_persistent_kernel<{tile['tile_x']},{tile['tile_y']},{tile['threads']},f32x4>",
                 "kernel_ms_mean": round(kernel_ms, 4), "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel_source_hash": khash}
 
@@ -310,6 +319,8 @@ def bench_ours(args, dist: Dist):
                                "one batched persistent launch per step",
                    "frames_per_gpu": N_FRAMES, "H": H_FULLHD, "W": W_FULLHD, "alpha": 2,
                    "mask": "secant tau=12", "compute": "fp32", "out": "f32x4",
+                   "tile": f"{tile['tile_x']}x{tile['tile_y']}, {tile['threads']}+32 threads, "
+                           f"{tile['stages']} stages" + ("" if (args.no_autotune or args.config) else " (autotuned)"),
                    "parallelism": f"frame-sharded x{dist.world} (no collective)",
                    "l2": f"inputs larger than L2 ({px_per_step * BYTES_PER_PX / 1e6:.0f} MB moved per step)"},
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
@@ -457,6 +468,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--frames", type=int, default=N_FRAMES,
                     help="frames per GPU (default 64; smaller only for profiling)")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--config", default="", help="tile_x,tile_y,threads,stages (skips the autotuner)")
     ap.add_argument("--skip-extra", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")

@@ -70,7 +70,7 @@ typedef enum {
   NRM_ERR_NO_DEVICE = 6    /* no CUDA device is visible */
 } nrm_status;
 
-/* Pinhole intrinsics in pixels (Section 2: f_x, f_y, o_x, o_y). */
+/* Pinhole intrinsics in pixels (Section 2: f_x, f_y, o_x, o_y); fx, fy > 0. */
 typedef struct {
   double fx, fy, cx, cy;
 } nrm_intrinsics;
@@ -149,9 +149,12 @@ NRM_API int nrm_backward(nrm_handle* h, const void* depth, const float* grad_nor
  * first device-side error since the last call) and clears it. */
 NRM_API int nrm_sync_status(nrm_handle* h);
 
-/* Launch geometry of the forward kernels. tile_x in {64, 128, 256}, tile_y in
- * {4, 8, 16, 32}, threads in {128, 256, 512}, stages in {2, 3, 4} (persistent
- * kernel only), ctas_per_sm 0 = as many as fit. */
+/* Launch geometry of the forward kernels. (tile_x, tile_y, threads) must be one
+ * of the compiled shapes: (128,16,256) (the default), (128,8,256), (128,32,256),
+ * (128,8,128), (128,16,128), (128,32,512), (128,64,512), (64,16,128),
+ * (64,32,256), (64,64,256). threads counts the compute threads; the persistent
+ * kernel adds one producer warp. stages in {2, 3, 4} (persistent kernel only);
+ * ctas_per_sm 0 = as many as fit. */
 typedef struct {
   int tile_x, tile_y, threads, stages, ctas_per_sm;
 } nrm_tile_config;

@@ -94,7 +94,7 @@ bool encode_depth_map(CUtensorMap* m, const void* base, int in_dtype, int W, int
   return r == CUDA_SUCCESS;
 }
 
-bool finite_positive(double v) { return std::isfinite(v) && v != 0.0; }
+bool finite_positive(double v) { return std::isfinite(v) && v > 0.0; }
 
 int pow2_align(uintptr_t v, int cap) {
   int a = 1;
@@ -155,7 +155,7 @@ int validate_params(const nrm_params& p) {
 
 int validate_intrinsics(const nrm_intrinsics& K) {
   if (!finite_positive(K.fx) || !finite_positive(K.fy) || !std::isfinite(K.cx) || !std::isfinite(K.cy))
-    return fail(NRM_ERR_INVALID_ARG, "intrinsics must be finite with nonzero fx, fy");
+    return fail(NRM_ERR_INVALID_ARG, "intrinsics must be finite with positive fx, fy");
   return NRM_OK;
 }
 
@@ -283,7 +283,8 @@ int configure(nrm_handle* h, const nrm_tile_config& c) {
   rc = set_smem_attr(ks->plain[out], pl);
   if (rc) return rc;
   int occ = 0;
-  NRM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks->persistent[out], c.threads, ps),
+  NRM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks->persistent[out],
+                                                         nrm::persistent_threads(c.threads), ps),
            "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (occ < 1) return fail(NRM_ERR_UNSUPPORTED, "persistent kernel does not fit on an SM");
   const int per_sm = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, occ) : occ;
@@ -322,7 +323,7 @@ int build_slot_graph(nrm_handle* h, Slot& s) {
   std::memset(&kp, 0, sizeof(kp));
   kp.func = const_cast<void*>(h->ks->persistent[h->p.out_dtype]);
   kp.gridDim = dim3(h->persistent_grid);
-  kp.blockDim = dim3(h->cfg.threads);
+  kp.blockDim = dim3(nrm::persistent_threads(h->cfg.threads));
   kp.sharedMemBytes = nrm::persistent_smem_bytes(h->cfg.tile_x, h->cfg.tile_y, h->p.alpha, h->cfg.stages);
   kp.kernelParams = kargs;
   cudaGraphNode_t kn;

@@ -1,8 +1,8 @@
 // Device building blocks of the sm_103a normal-estimation kernels:
-// inline-PTX wrappers for mbarrier and TMA (cp.async.bulk.tensor), bounded
-// waits, the per-pixel closed form (Eq. 4-6 of arXiv 2209.08241) with the
-// Section 3.2 mask, and the tile loop shared by the plain and persistent
-// forward kernels.
+// inline-PTX wrappers for mbarrier, named barriers and TMA
+// (cp.async.bulk.tensor), bounded waits, depth decoding, the per-pixel closed
+// form (Eq. 4-6 of arXiv 2209.08241) with the Section 3.2 mask, and the tile
+// loop shared by the plain and persistent forward kernels.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -34,12 +34,6 @@ __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Orders this thread's earlier generic-proxy shared-memory accesses before
-// later async-proxy (TMA) accesses.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 // Acquire fence for a tensor map that the host wrote to global memory.
 __device__ __forceinline__ void fence_tensormap_acquire(const void* tmap) {
   asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
@@ -54,14 +48,18 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// Tests phase `parity` for completion. A thread whose phase is not complete
+// is suspended by the hardware until the phase completes or about
+// kSuspendHintNs elapse, so a waiting warp does not spin on issue slots.
+constexpr uint32_t kSuspendHintNs = 1000000;
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(kSuspendHintNs)
       : "memory");
   return ok != 0;
 }
@@ -90,15 +88,36 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int 
       : "memory");
 }
 
+// Named barrier over `count` threads (a multiple of 32) that also ORs a
+// predicate across them.
+__device__ __forceinline__ bool bar_red_or(uint32_t id, uint32_t count, bool pred) {
+  uint32_t out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(out)
+      : "r"((uint32_t)pred), "r"(id), "r"(count)
+      : "memory");
+  return out != 0;
+}
+
+// Hardware reciprocal square root, flush-to-zero (inputs here are >= FLT_MIN).
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ void record_error(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
-// ------------------------------------------------------ per-pixel method
+// -------------------------------------------------- per-pixel (adjoint path)
 
-// Depth element decoding. f32: metres, valid iff positive and finite.
-// u16: raw units (the frame constants carry depth_scale^2), valid iff != 0.
-// Sums and differences of u16 are formed exactly in integers (|.| < 2^17).
+// Depth validity and stencil sums for the adjoint kernel (float32 metres,
+// valid iff positive and finite).
 struct StencilSums {
   float S24, D24, S35, D35;
   bool ok;
@@ -118,18 +137,6 @@ __device__ __forceinline__ StencilSums stencil_sums(const float* p, int alpha, i
   return s;
 }
 
-__device__ __forceinline__ StencilSums stencil_sums(const uint16_t* p, int alpha, int bw) {
-  const int d1 = p[0], d2 = p[alpha], d4 = p[-alpha];
-  const int d3 = p[alpha * bw], d5 = p[-alpha * bw];
-  StencilSums s;
-  s.ok = (d1 != 0) & (d2 != 0) & (d3 != 0) & (d4 != 0) & (d5 != 0);
-  s.S24 = (float)(d2 + d4);
-  s.D24 = (float)(d2 - d4);
-  s.S35 = (float)(d3 + d5);
-  s.D35 = (float)(d3 - d5);
-  return s;
-}
-
 struct FrameConsts {
   float a, b, c, inv_fx, inv_fy, cx, cy;
 };
@@ -145,230 +152,7 @@ __device__ __forceinline__ void closed_form_normal(const StencilSums& s, const F
   nz = fmaf(-u1, nx, fmaf(-v1, ny, P));
 }
 
-// Section 3.2 mask, compared in squared form (no square root):
-//   RAW:    ||n|| <= tau                  <=>  q <= tau^2
-//   SECANT: ||n|| ||ray|| / P <= tau      <=>  q ray2 <= tau^2 P^2   (P > 0)
-__device__ __forceinline__ bool keep_pixel(bool ok, float q, float P, float ray2, int mode,
-                                           float tau2) {
-  if (mode == NRM_MASK_RAW) return ok && q > 0.0f && q <= tau2;
-  return ok && P > 0.0f && q * ray2 <= tau2 * (P * P);
-}
-
-// Expands the low `n` bits of b into n bytes of value 0/1 (n = 2 or 4).
-__device__ __forceinline__ uint32_t bits_to_bytes4(uint32_t b) {
-  return (b * 0x00204081u) & 0x01010101u;
-}
-
-// --------------------------------------------------------- tile compute
-
-// The frame fields the tile loop needs, read once per tile into registers.
-// The orientation sign is folded into the Eq. 4-6 constants: the normal is
-// linear in (a, b, c), so scaling them by -1 negates n and leaves q = n . n
-// and P^2 unchanged.
-struct TileFrame {
-  float a, b, c, inv_fx, inv_fy, cx, cy;
-  int H, W;
-  long long out_pitch;
-  void* normals;
-  uint8_t* valid;
-  int mask_align;
-};
-
-__device__ __forceinline__ TileFrame tile_frame(const FrameDesc& fd, float sign) {
-  TileFrame f;
-  f.a = -sign * fd.a;  // n_x = -a S35 D24  ->  (A S35) D24 with A = -sign a
-  f.b = -sign * fd.b;
-  f.c = sign * fd.c;
-  f.inv_fx = fd.inv_fx;
-  f.inv_fy = fd.inv_fy;
-  f.cx = fd.cx;
-  f.cy = fd.cy;
-  f.H = fd.H;
-  f.W = fd.W;
-  f.out_pitch = fd.out_pitch;
-  f.normals = fd.normals;
-  f.valid = fd.valid;
-  f.mask_align = fd.mask_align;
-  return f;
-}
-
-// Decodes one staged depth element to float; an invalid depth becomes NaN so
-// that every quantity computed from it is NaN and fails the mask comparison.
-// float32: valid iff 0 < d <= FLT_MAX, i.e. bits - 1 < 0x7F7FFFFF (unsigned).
-__device__ __forceinline__ float decode_depth(float d) {
-  return (__float_as_uint(d) - 1u) < 0x7F7FFFFFu ? d : __int_as_float(0x7fc00000);
-}
-// uint16: exact conversion (2^23 + u is representable; subtracting 2^23 is
-// exact); raw 0 is invalid. The depth scale is folded into a, b, c.
-__device__ __forceinline__ float decode_depth_u16(uint32_t u) {
-  const float f = __uint_as_float(0x4B000000u | u) - 8388608.0f;
-  return u != 0u ? f : __int_as_float(0x7fc00000);
-}
-
-// Staged tile (TMA box, native dtype) -> decoded float tile, n elements
-// (a multiple of 4; both buffers 16-byte aligned).
-template <int NT>
-__device__ __forceinline__ void decode_tile(const float* __restrict__ src, float* __restrict__ dst, int n) {
-  for (int i = threadIdx.x * 4; i < n; i += NT * 4) {
-    float4 v = *reinterpret_cast<const float4*>(src + i);
-    v.x = decode_depth(v.x);
-    v.y = decode_depth(v.y);
-    v.z = decode_depth(v.z);
-    v.w = decode_depth(v.w);
-    *reinterpret_cast<float4*>(dst + i) = v;
-  }
-}
-
-template <int NT>
-__device__ __forceinline__ void decode_tile(const uint16_t* __restrict__ src, float* __restrict__ dst, int n) {
-  for (int i = threadIdx.x * 4; i < n; i += NT * 4) {
-    const uint2 r = *reinterpret_cast<const uint2*>(src + i);
-    float4 v;
-    v.x = decode_depth_u16(r.x & 0xFFFFu);
-    v.y = decode_depth_u16(r.x >> 16);
-    v.z = decode_depth_u16(r.y & 0xFFFFu);
-    v.w = decode_depth_u16(r.y >> 16);
-    *reinterpret_cast<float4*>(dst + i) = v;
-  }
-}
-
-// Plain-load path (frames whose base or pitch rules out TMA): reads the halo
-// box straight from global memory into the decoded float tile; outside the
-// image counts as invalid, exactly like the TMA zero fill.
-template <typename InT>
-__device__ __forceinline__ void load_tile_decoded(float* dst, int bw, int bh, const FrameDesc& fd, int x0,
-                                                  int y0) {
-  const InT* src = reinterpret_cast<const InT*>(fd.depth);
-  const int n = bw * bh;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int ly = i / bw, lx = i - ly * bw;
-    const int x = x0 + lx, y = y0 + ly;
-    float v = __int_as_float(0x7fc00000);
-    if (x >= 0 && y >= 0 && x < fd.W && y < fd.H) {
-      const InT raw = __ldg(src + (long long)y * fd.depth_pitch + x);
-      if constexpr (sizeof(InT) == 2)
-        v = decode_depth_u16(raw);
-      else
-        v = decode_depth(raw);
-    }
-    dst[i] = v;
-  }
-}
-
-// Computes one TX x TY output tile from the decoded float halo tile F
-// (origin global (gx0 - padx, gy0 - alpha), row pitch bw).
-// Warp w handles rows w, w + NW, ...; lane l handles columns 32 k + l, so each
-// store instruction of a warp covers 32 consecutive pixels (512 B of float4).
-// Per-column terms (u1, 1 + u1^2) are computed once per tile. Mask bytes are
-// gathered with one ballot per 32 pixels and written as TX/32 consecutive bytes
-// per lane.
-template <int TX, int TY, int NT, bool HALF, bool SECANT>
-__device__ __forceinline__ void compute_tile(const float* __restrict__ F, int bw, int padx,
-                                             const TileFrame& f, int gx0, int gy0, int alpha,
-                                             float tau2) {
-  constexpr int NW = NT / 32;
-  constexpr int CH = TX / 32;
-  static_assert(TY % NW == 0, "rows must divide among warps");
-  static_assert(CH == 2 || CH == 4, "TX must be 64 or 128");
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-
-  float u1[CH], ku[CH];
-  bool colok[CH];
-#pragma unroll
-  for (int c = 0; c < CH; ++c) {
-    const int gx = gx0 + 32 * c + lane;
-    u1[c] = ((float)gx - f.cx) * f.inv_fx;
-    ku[c] = fmaf(u1[c], u1[c], 1.0f);
-    colok[c] = gx < f.W;
-  }
-  const int dv = alpha * bw;
-
-#pragma unroll 1
-  for (int ly = warp; ly < TY; ly += NW) {
-    const int gy = gy0 + ly;
-    if (gy >= f.H) break;
-    const float v1 = ((float)gy - f.cy) * f.inv_fy;
-    const float kv = v1 * v1;
-    const float* row = F + (ly + alpha) * bw + padx + lane;
-    const long long out_row = (long long)gy * f.out_pitch + gx0 + lane;
-    uint32_t ballots[CH];
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const float* p = row + 32 * c;
-      const float d1 = p[0];
-      const float d2 = p[alpha], d4 = p[-alpha];
-      const float d3 = p[dv], d5 = p[-dv];
-      // Eq. 4-6 (Section 3.1).
-      const float S24 = d2 + d4, D24 = d2 - d4;
-      const float S35 = d3 + d5, D35 = d3 - d5;
-      const float nx = (f.a * S35) * D24;
-      const float ny = (f.b * S24) * D35;
-      const float P = (f.c * S24) * S35;  // n . (u1, v1, 1) (times the sign)
-      const float nz = fmaf(-u1[c], nx, fmaf(-v1, ny, P));
-      const float q = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
-      // Section 3.2 mask in squared form; NaN (invalid depth) fails every test.
-      bool keep = colok[c] && (d1 == d1) && (q > 0.0f);
-      if (SECANT)
-        keep = keep && (q * (ku[c] + kv) <= tau2 * (P * P));
-      else
-        keep = keep && (q <= tau2);
-      // Select, not multiply: n is NaN next to invalid depths.
-      const float inv = rsqrtf(q);
-      const float ox = keep ? nx * inv : 0.0f;
-      const float oy = keep ? ny * inv : 0.0f;
-      const float oz = keep ? nz * inv : 0.0f;
-      ballots[c] = __ballot_sync(0xffffffffu, keep);
-      if (colok[c]) {
-        if (HALF) {
-          __half2 xy = __floats2half2_rn(ox, oy);
-          __half2 zw = __floats2half2_rn(oz, 0.0f);
-          uint2 v;
-          v.x = *reinterpret_cast<uint32_t*>(&xy);
-          v.y = *reinterpret_cast<uint32_t*>(&zw);
-          __stcs(reinterpret_cast<uint2*>(f.normals) + out_row + 32 * c, v);
-        } else {
-          __stcs(reinterpret_cast<float4*>(f.normals) + out_row + 32 * c, make_float4(ox, oy, oz, 0.0f));
-        }
-      }
-    }
-    // Mask: lane l owns tile columns [CH l, CH l + CH).
-    const int first = CH * lane;
-    const int cidx = first >> 5;
-    uint32_t word = 0;
-#pragma unroll
-    for (int c = 0; c < CH; ++c) word = (c == cidx) ? ballots[c] : word;
-    const uint32_t bits = (word >> (first & 31)) & ((1u << CH) - 1u);
-    const int gx = gx0 + first;
-    uint8_t* mrow = f.valid + (long long)gy * f.out_pitch;
-    if (gx + CH <= f.W && f.mask_align >= CH) {
-      if (CH == 2) {
-        const uint32_t v = bits_to_bytes4(bits);
-        __stcs(reinterpret_cast<unsigned short*>(mrow + gx), (unsigned short)v);
-      } else {
-        __stcs(reinterpret_cast<unsigned int*>(mrow + gx), bits_to_bytes4(bits));
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < CH; ++j) {
-        if (gx + j < f.W) mrow[gx + j] = (uint8_t)((bits >> j) & 1u);
-      }
-    }
-  }
-}
-
-// Both mask modes of compute_tile, chosen once per tile.
-template <int TX, int TY, int NT, bool HALF>
-__device__ __forceinline__ void compute_tile_any(const float* __restrict__ F, int bw, int padx,
-                                                 const TileFrame& f, int gx0, int gy0, const Globals& g) {
-  if (g.mask_mode == NRM_MASK_SECANT)
-    compute_tile<TX, TY, NT, HALF, true>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
-  else
-    compute_tile<TX, TY, NT, HALF, false>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
-}
-
-// Loads the halo tile with plain loads (frames whose base or pitch rules out
-// TMA), zero-filling outside the image exactly as the TMA out-of-bounds fill.
+// Loads a halo box with plain loads, zero-filling outside the image.
 template <typename InT>
 __device__ __forceinline__ void load_tile_plain(InT* sm, int bw, int bh, const FrameDesc& fd,
                                                 int x0, int y0) {
@@ -383,8 +167,272 @@ __device__ __forceinline__ void load_tile_plain(InT* sm, int bw, int bh, const F
   }
 }
 
-// Geometry of a frame's halo box for the forward kernels.
-__device__ __forceinline__ int elem_bytes(int in_dtype) { return in_dtype == NRM_IN_U16_MM ? 2 : 4; }
+// ------------------------------------------------------------ forward tiles
+
+// Everything the forward tile loop needs about a frame, in registers. The
+// orientation sign is folded into the Eq. 4-6 constants: the normal is linear
+// in (a, b, c), so scaling them by -1 negates n and leaves q = n . n and P^2
+// unchanged.
+struct TileFrame {
+  float a, b, c;           // n_x = (a S35) D24, n_y = (b S24) D35, P = (c S24) S35
+  float inv_fx, inv_fy, cx, cy;
+  int H, W;
+  int mask_align;
+  int in_dtype;
+  long long out_pitch;
+  void* normals;
+  uint8_t* valid;
+  const void* depth;
+  long long depth_pitch;
+};
+
+__device__ __forceinline__ TileFrame tile_frame(const FrameDesc& fd, float sign) {
+  TileFrame f;
+  f.a = -sign * fd.a;
+  f.b = -sign * fd.b;
+  f.c = sign * fd.c;
+  f.inv_fx = fd.inv_fx;
+  f.inv_fy = fd.inv_fy;
+  f.cx = fd.cx;
+  f.cy = fd.cy;
+  f.H = fd.H;
+  f.W = fd.W;
+  f.mask_align = fd.mask_align;
+  f.in_dtype = fd.in_dtype;
+  f.out_pitch = fd.out_pitch;
+  f.normals = fd.normals;
+  f.valid = fd.valid;
+  f.depth = fd.depth;
+  f.depth_pitch = fd.depth_pitch;
+  return f;
+}
+
+// Decodes one staged depth element to float; an invalid depth becomes NaN so
+// that every quantity computed from it is NaN and fails the mask comparison.
+// float32: valid iff 0 < d <= FLT_MAX, i.e. bits - 1 < 0x7F7FFFFF (unsigned).
+__device__ __forceinline__ float decode_depth(float d) {
+  return (__float_as_uint(d) - 1u) < 0x7F7FFFFFu ? d : __int_as_float(0x7fc00000);
+}
+// uint16 (u < 2^16): for u >= 1 the bits (u - 1) | 0x4B000000 encode the float
+// 2^23 + u - 1 exactly, and subtracting 2^23 - 1 gives u exactly; for the
+// invalid raw value 0 they are 0xFFFFFFFF, a NaN, which the subtraction
+// keeps. The depth scale is folded into a, b, c.
+__device__ __forceinline__ float decode_depth_u16(uint32_t u) {
+  return __uint_as_float((u - 1u) | 0x4B000000u) - 8388607.0f;
+}
+
+// Staged tile (TMA box, native dtype) -> decoded float tile, by threads
+// 0..NT-1. The float tile always has the float32 geometry: pitch
+// fw = TX + 2 pad_x(alpha, 4) (a multiple of 4), origin gx0 - pad_x(alpha, 4);
+// a uint16 box is wider (pad_x(alpha, 2) >= pad_x(alpha, 4)), so its columns
+// are read from offset `skip` = pad_x(alpha, 2) - pad_x(alpha, 4) (a multiple
+// of 4). Work is in groups of 4 consecutive elements of one row.
+template <int NT>
+__device__ __forceinline__ void decode_tile(const float* __restrict__ src, float* __restrict__ dst, int fw,
+                                            int rows, int /*src_pitch*/, int /*skip*/) {
+  const int n = fw * rows;  // same geometry: a flat copy
+  for (int i = threadIdx.x * 4; i < n; i += NT * 4) {
+    float4 v = *reinterpret_cast<const float4*>(src + i);
+    v.x = decode_depth(v.x);
+    v.y = decode_depth(v.y);
+    v.z = decode_depth(v.z);
+    v.w = decode_depth(v.w);
+    *reinterpret_cast<float4*>(dst + i) = v;
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ void decode_tile(const uint16_t* __restrict__ src, float* __restrict__ dst, int fw,
+                                            int rows, int src_pitch, int skip) {
+  const int gpr = fw >> 2;  // 4-element groups per row
+  const int n = gpr * rows;
+  for (int gi = threadIdx.x; gi < n; gi += NT) {
+    const int r = gi / gpr;
+    const int c = (gi - r * gpr) << 2;
+    const uint2 raw = *reinterpret_cast<const uint2*>(src + r * src_pitch + skip + c);
+    float4 v;
+    v.x = decode_depth_u16(raw.x & 0xFFFFu);
+    v.y = decode_depth_u16(raw.x >> 16);
+    v.z = decode_depth_u16(raw.y & 0xFFFFu);
+    v.w = decode_depth_u16(raw.y >> 16);
+    *reinterpret_cast<float4*>(dst + r * fw + c) = v;
+  }
+}
+
+// Plain-load path (frames whose base or pitch rules out TMA): reads the halo
+// box straight from global memory into the decoded float tile, by threads
+// 0..NT-1; outside the image counts as invalid, exactly like the TMA zero fill.
+template <typename InT, int NT>
+__device__ __forceinline__ void load_tile_decoded(float* dst, int bw, int bh, const TileFrame& f, int x0,
+                                                  int y0) {
+  const InT* src = reinterpret_cast<const InT*>(f.depth);
+  const int n = bw * bh;
+  for (int i = threadIdx.x; i < n; i += NT) {
+    const int ly = i / bw, lx = i - ly * bw;
+    const int x = x0 + lx, y = y0 + ly;
+    float v = __int_as_float(0x7fc00000);
+    if (x >= 0 && y >= 0 && x < f.W && y < f.H) {
+      const InT raw = __ldg(src + (long long)y * f.depth_pitch + x);
+      if constexpr (sizeof(InT) == 2)
+        v = decode_depth_u16(raw);
+      else
+        v = decode_depth(raw);
+    }
+    dst[i] = v;
+  }
+}
+
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+
+// Expands the low 2 or 4 bits of b into bytes of value 0/1.
+__device__ __forceinline__ uint32_t bits_to_bytes4(uint32_t b) {
+  return (b * 0x00204081u) & 0x01010101u;
+}
+
+// Computes one TX x TY output tile from the decoded float halo tile F
+// (origin global (gx0 - padx, gy0 - alpha), row pitch bw), threads 0..NT-1.
+// Warp w handles rows w, w + NW, ...; lane l handles columns 32 k + l, so each
+// store instruction of a warp covers 32 consecutive pixels (512 B of float4).
+// Pixels 32 k + l and 32 (k+1) + l are evaluated as a pair with the paired
+// FP32 instructions (FADD2 / FMUL2 / FFMA2), whose per-lane results are those
+// of the scalar operations. Per-column terms are computed once per tile. Mask
+// bytes are gathered with one ballot per 32 pixels and written as TX/32
+// consecutive bytes per lane.
+template <int TX, int TY, int NT, bool HALF, bool SECANT, bool FULL>
+__device__ __forceinline__ void compute_tile(const float* __restrict__ F, int bw, int padx,
+                                             const TileFrame& f, int gx0, int gy0, int alpha,
+                                             float tau2) {
+  constexpr int NW = NT / 32;
+  constexpr int CH = TX / 32;
+  constexpr int NP = CH / 2;
+  static_assert(TY % NW == 0, "rows must divide among warps");
+  static_assert(CH == 2 || CH == 4, "TX must be 64 or 128");
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const float kFltMin = 1.17549435e-38f;
+
+  float2 nu1[NP], ku[NP];
+  bool colok[CH];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int gxa = gx0 + 64 * p + lane, gxb = gxa + 32;
+    const float ua = ((float)gxa - f.cx) * f.inv_fx;
+    const float ub = ((float)gxb - f.cx) * f.inv_fx;
+    nu1[p] = f2(-ua, -ub);
+    ku[p] = f2(fmaf(ua, ua, 1.0f), fmaf(ub, ub, 1.0f));
+    colok[2 * p] = FULL || gxa < f.W;
+    colok[2 * p + 1] = FULL || gxb < f.W;
+  }
+  const float2 A = f2(f.a, f.a), B = f2(f.b, f.b), C = f2(f.c, f.c), T = f2(tau2, tau2);
+  const float2 M1 = f2(-1.0f, -1.0f);
+  const int dv = alpha * bw;
+
+#pragma unroll 1
+  for (int ly = warp; ly < TY; ly += NW) {
+    const int gy = gy0 + ly;
+    if (gy >= f.H) break;
+    const float v1 = ((float)gy - f.cy) * f.inv_fy;
+    const float2 nv1 = f2(-v1, -v1);
+    const float2 kv = f2(v1 * v1, v1 * v1);
+    const float* row = F + (ly + alpha) * bw + padx + lane;
+    const long long out_row = (long long)gy * f.out_pitch + gx0 + lane;
+    uint32_t ballots[CH];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const float* pa = row + 64 * p;
+      const float* pb = pa + 32;
+      const float2 d1 = f2(pa[0], pb[0]);
+      const float2 d2 = f2(pa[alpha], pb[alpha]);
+      const float2 d4 = f2(pa[-alpha], pb[-alpha]);
+      const float2 d3 = f2(pa[dv], pb[dv]);
+      const float2 d5 = f2(pa[-dv], pb[-dv]);
+      // Eq. 4-6 (Section 3.1).
+      // d2 - d4 as one fused (-1) d4 + d2: a single rounding, like a subtraction.
+      const float2 S24 = __fadd2_rn(d2, d4), D24 = __ffma2_rn(M1, d4, d2);
+      const float2 S35 = __fadd2_rn(d3, d5), D35 = __ffma2_rn(M1, d5, d3);
+      const float2 nx = __fmul2_rn(__fmul2_rn(A, S35), D24);
+      const float2 ny = __fmul2_rn(__fmul2_rn(B, S24), D35);
+      const float2 P = __fmul2_rn(__fmul2_rn(C, S24), S35);  // n . (u1, v1, 1), times the sign
+      const float2 nz = __ffma2_rn(nu1[p], nx, __ffma2_rn(nv1, ny, P));
+      const float2 q = __ffma2_rn(nx, nx, __ffma2_rn(ny, ny, __fmul2_rn(nz, nz)));
+      // Section 3.2 mask in squared form; NaN (invalid depth) fails every test.
+      // (Bitwise &: every operand is side-effect free, and no branches.)
+      bool ka = colok[2 * p] & (d1.x == d1.x) & (q.x >= kFltMin);
+      bool kb = colok[2 * p + 1] & (d1.y == d1.y) & (q.y >= kFltMin);
+      if (SECANT) {
+        const float2 lhs = __fmul2_rn(q, __fadd2_rn(ku[p], kv));
+        const float2 rhs = __fmul2_rn(T, __fmul2_rn(P, P));
+        ka = ka & (lhs.x <= rhs.x);
+        kb = kb & (lhs.y <= rhs.y);
+      } else {
+        ka = ka & (q.x <= tau2);
+        kb = kb & (q.y <= tau2);
+      }
+      const float2 inv = f2(rsqrt_ftz(q.x), rsqrt_ftz(q.y));
+      const float2 ox = __fmul2_rn(nx, inv), oy = __fmul2_rn(ny, inv), oz = __fmul2_rn(nz, inv);
+      // Select, not multiply: n is NaN next to invalid depths.
+      const float4 va = ka ? make_float4(ox.x, oy.x, oz.x, 0.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 vb = kb ? make_float4(ox.y, oy.y, oz.y, 0.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
+      ballots[2 * p] = __ballot_sync(0xffffffffu, ka);
+      ballots[2 * p + 1] = __ballot_sync(0xffffffffu, kb);
+      if (HALF) {
+        const __half2 xya = __floats2half2_rn(va.x, va.y), zwa = __floats2half2_rn(va.z, 0.0f);
+        const __half2 xyb = __floats2half2_rn(vb.x, vb.y), zwb = __floats2half2_rn(vb.z, 0.0f);
+        uint2* dst = reinterpret_cast<uint2*>(f.normals) + out_row + 64 * p;
+        if (FULL || colok[2 * p])
+          __stcs(dst, make_uint2(*reinterpret_cast<const uint32_t*>(&xya), *reinterpret_cast<const uint32_t*>(&zwa)));
+        if (FULL || colok[2 * p + 1])
+          __stcs(dst + 32,
+                 make_uint2(*reinterpret_cast<const uint32_t*>(&xyb), *reinterpret_cast<const uint32_t*>(&zwb)));
+      } else {
+        float4* dst = reinterpret_cast<float4*>(f.normals) + out_row + 64 * p;
+        if (FULL || colok[2 * p]) __stcs(dst, va);
+        if (FULL || colok[2 * p + 1]) __stcs(dst + 32, vb);
+      }
+    }
+    // Mask: lane l owns tile columns [CH l, CH l + CH).
+    const int first = CH * lane;
+    const int cidx = first >> 5;
+    uint32_t word = 0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) word = (c == cidx) ? ballots[c] : word;
+    const uint32_t bits = (word >> (first & 31)) & ((1u << CH) - 1u);
+    const int gx = gx0 + first;
+    uint8_t* mrow = f.valid + (long long)gy * f.out_pitch;
+    if ((FULL || gx + CH <= f.W) && f.mask_align >= CH) {
+      if (CH == 2) {
+        __stcs(reinterpret_cast<unsigned short*>(mrow + gx), (unsigned short)bits_to_bytes4(bits));
+      } else {
+        __stcs(reinterpret_cast<unsigned int*>(mrow + gx), bits_to_bytes4(bits));
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        if (gx + j < f.W) mrow[gx + j] = (uint8_t)((bits >> j) & 1u);
+      }
+    }
+  }
+}
+
+// compute_tile for the tile's mask mode, with the column checks compiled out
+// for tiles that lie entirely inside the image width (all but the last tile
+// column of a frame whose width is not a multiple of TX).
+template <int TX, int TY, int NT, bool HALF>
+__device__ __forceinline__ void compute_tile_any(const float* __restrict__ F, int bw, int padx,
+                                                 const TileFrame& f, int gx0, int gy0, const Globals& g) {
+  const bool full = gx0 + TX <= f.W;
+  if (g.mask_mode == NRM_MASK_SECANT) {
+    if (full)
+      compute_tile<TX, TY, NT, HALF, true, true>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
+    else
+      compute_tile<TX, TY, NT, HALF, true, false>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
+  } else {
+    if (full)
+      compute_tile<TX, TY, NT, HALF, false, true>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
+    else
+      compute_tile<TX, TY, NT, HALF, false, false>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
+  }
+}
 
 }  // namespace dev
 }  // namespace nrm

@@ -4,18 +4,29 @@
 // Both kernels stage a halo tile of depth, (TX + 2 pad) x (TY + 2 alpha), into
 // shared memory with one 2-D TMA load (cp.async.bulk.tensor, mbarrier
 // completion; the tensor map's out-of-bounds zero fill doubles as "invalid
-// depth" at the image border), then every thread evaluates its pixels from
-// shared memory and streams float4/half4 normals and packed mask bytes out.
+// depth" at the image border), decode it once into a float tile (invalid
+// depth -> NaN), then every compute thread evaluates its pixels from shared
+// memory and streams float4/half4 normals and packed mask bytes out.
 //
 //  fwd_plain_kernel       one CTA per tile of one frame (the per-frame launch);
 //  fwd_persistent_kernel  a persistent grid walks the (frame, tile) work list of
-//                         a whole batch with an S-stage TMA pipeline: while a
-//                         tile is computed, the next S-1 tiles are in flight.
+//                         a whole batch. One producer warp walks the list,
+//                         stages each tile's frame data in shared memory and
+//                         issues the TMA loads into an S-stage ring (full/empty
+//                         mbarriers); the NT compute threads decode and compute,
+//                         synchronising only among themselves (named barrier 1).
 #include "nrm_device.cuh"
 
 namespace nrm {
 
 using namespace dev;
+
+// Per-stage tile record written by the producer, read by the compute threads.
+struct alignas(16) StageInfo {
+  TileFrame f;
+  int tx, ty, tma, frame;
+};
+static_assert(sizeof(StageInfo) <= kStageInfoBytes, "StageInfo must fit its slot");
 
 template <int TX, int TY, int NT, bool HALF>
 __global__ void __launch_bounds__(NT)
@@ -24,14 +35,17 @@ __global__ void __launch_bounds__(NT)
   const int alpha = g.alpha;
   const bool u16 = fd.in_dtype == NRM_IN_U16_MM;
   const int eb = u16 ? 2 : 4;
-  const int padx = pad_x(alpha, eb);
+  const int padx = pad_x(alpha, eb);  // staging (TMA) box
   const int bw = TX + 2 * padx;
+  const int pad4 = pad_x(alpha, 4);   // decoded float tile
+  const int fw = TX + 2 * pad4;
   const int bh = TY + 2 * alpha;
   const int gx0 = blockIdx.x * TX;
   const int gy0 = blockIdx.y * TY;
   const unsigned SB = stage_bytes_for(TX, TY, alpha);
   float* F = reinterpret_cast<float*>(smem + SB);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SB + ftile_bytes_for(TX, TY, alpha));
+  const TileFrame tf = tile_frame(fd, g.sign);
 
   bool ok = true;
   if (fd.use_tma) {
@@ -48,15 +62,15 @@ __global__ void __launch_bounds__(NT)
     ok = mbar_wait_bounded(b, 0, g.timeout_ns);
     if (ok) {
       if (u16)
-        decode_tile<NT>(reinterpret_cast<const uint16_t*>(smem), F, bw * bh);
+        decode_tile<NT>(reinterpret_cast<const uint16_t*>(smem), F, fw, bh, bw, padx - pad4);
       else
-        decode_tile<NT>(reinterpret_cast<const float*>(smem), F, bw * bh);
+        decode_tile<NT>(reinterpret_cast<const float*>(smem), F, fw, bh, bw, 0);
     }
   } else {
     if (u16)
-      load_tile_decoded<uint16_t>(F, bw, bh, fd, gx0 - padx, gy0 - alpha);
+      load_tile_decoded<uint16_t, NT>(F, fw, bh, tf, gx0 - pad4, gy0 - alpha);
     else
-      load_tile_decoded<float>(F, bw, bh, fd, gx0 - padx, gy0 - alpha);
+      load_tile_decoded<float, NT>(F, fw, bh, tf, gx0 - pad4, gy0 - alpha);
   }
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) {
@@ -65,11 +79,12 @@ __global__ void __launch_bounds__(NT)
     }
     return;
   }
-  compute_tile_any<TX, TY, NT, HALF>(F, bw, padx, tile_frame(fd, g.sign), gx0, gy0, g);
+  compute_tile_any<TX, TY, NT, HALF>(F, fw, pad4, tf, gx0, gy0, g);
 }
 
+// Block = NT compute threads + one producer warp.
 template <int TX, int TY, int NT, bool HALF>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT + 32)
     fwd_persistent_kernel(const BatchArgs args, const Globals g) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int S = args.stages;
@@ -77,8 +92,9 @@ __global__ void __launch_bounds__(NT)
   const int alpha = g.alpha;
   const unsigned FB = ftile_bytes_for(TX, TY, alpha);
   unsigned char* fbase = smem + (size_t)S * SB;  // two decoded tiles of FB bytes
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * SB + 2 * FB);
-  int4* info = reinterpret_cast<int4*>(smem + (size_t)S * SB + 2 * FB + 128);
+  uint64_t* full = reinterpret_cast<uint64_t*>(fbase + 2 * FB);
+  uint64_t* empty = full + S;
+  StageInfo* info = reinterpret_cast<StageInfo*>(fbase + 2 * FB + 128);
   const int total = args.hdr->total_tiles;
   const int nf = args.hdr->n_frames;
   const int G = (int)gridDim.x;
@@ -86,86 +102,96 @@ __global__ void __launch_bounds__(NT)
   if (my == 0) return;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
     fence_barrier_init();
   }
   __syncthreads();
 
-  // Producer state (thread 0 only): frame cursor over the work list (this
-  // CTA's tiles increase monotonically), last fenced tensor map, tiles issued.
-  int cur = 0;
-  int fenced = -1;
-  int issued = 0;
-  auto issue = [&](int j) {
-    const int t = (int)blockIdx.x + j * G;
-    while (cur + 1 < nf && __ldg(args.tile_begin + cur + 1) <= t) ++cur;
-    const FrameDesc* fd = args.frames + cur;
-    const int local = t - __ldg(args.tile_begin + cur);
-    const int tiles_x = fd->tiles_x;
-    const int ty = local / tiles_x;
-    const int tx = local - ty * tiles_x;
-    const int s = j % S;
-    const int tma = fd->use_tma;
-    info[s] = make_int4(cur, tx, ty, tma);
-    const uint32_t bar = smem_u32(&bars[s]);
-    if (tma) {
-      if (cur != fenced) {
-        fence_tensormap_acquire(&fd->tmap);
-        fenced = cur;
+  if (threadIdx.x >= NT) {
+    // ------------------------------------------------------------ producer
+    if (threadIdx.x != NT) return;
+    int cur = 0;      // frame cursor: this CTA's tiles increase monotonically
+    int fenced = -1;  // last tensor map fenced
+    for (int j = 0; j < my; ++j) {
+      const int s = j % S;
+      if (j >= S &&
+          !mbar_wait_bounded(smem_u32(&empty[s]), (uint32_t)(((j / S) - 1) & 1), g.timeout_ns)) {
+        record_error(g.status, NRM_ERR_TIMEOUT);
+        // Let every copy this warp issued land before the CTA can exit.
+        for (int k = j - S; k < j; ++k)
+          mbar_wait_bounded(smem_u32(&full[k % S]), (uint32_t)((k / S) & 1), g.timeout_ns);
+        return;
       }
-      const int eb = fd->in_dtype == NRM_IN_U16_MM ? 2 : 4;
-      const int padx = pad_x(alpha, eb);
-      mbar_arrive_expect_tx(bar, (uint32_t)((TX + 2 * padx) * (TY + 2 * alpha) * eb));
-      tma_load_2d(smem_u32(smem + (size_t)s * SB), &fd->tmap, tx * TX - padx, ty * TY - alpha, bar);
-    } else {
-      mbar_arrive(bar);  // plain-load tile: the consumers read global memory themselves
+      const int t = (int)blockIdx.x + j * G;
+      while (cur + 1 < nf && __ldg(args.tile_begin + cur + 1) <= t) ++cur;
+      const FrameDesc* fd = args.frames + cur;
+      const int local = t - __ldg(args.tile_begin + cur);
+      const int tiles_x = fd->tiles_x;
+      const int ty = local / tiles_x;
+      const int tx = local - ty * tiles_x;
+      StageInfo& si = info[s];
+      si.f = tile_frame(*fd, g.sign);
+      si.tx = tx;
+      si.ty = ty;
+      si.tma = fd->use_tma;
+      si.frame = cur;
+      const uint32_t bar = smem_u32(&full[s]);
+      if (si.tma) {
+        if (cur != fenced) {
+          fence_tensormap_acquire(&fd->tmap);
+          fenced = cur;
+        }
+        const int eb = si.f.in_dtype == NRM_IN_U16_MM ? 2 : 4;
+        const int padx = pad_x(alpha, eb);
+        mbar_arrive_expect_tx(bar, (uint32_t)((TX + 2 * padx) * (TY + 2 * alpha) * eb));
+        tma_load_2d(smem_u32(smem + (size_t)s * SB), &fd->tmap, tx * TX - padx, ty * TY - alpha, bar);
+      } else {
+        mbar_arrive(bar);  // plain-load tile: the compute threads read global memory themselves
+      }
     }
-    ++issued;
-  };
-
-  if (threadIdx.x == 0) {
-    for (int j = 0; j < S && j < my; ++j) issue(j);
+    return;
   }
 
+  // -------------------------------------------------------------- compute
   for (int i = 0; i < my; ++i) {
     const int s = i % S;
-    const bool ok = mbar_wait_bounded(smem_u32(&bars[s]), (uint32_t)((i / S) & 1), g.timeout_ns);
-    const int4 si = info[s];
-    const FrameDesc& fd = args.frames[si.x];
-    const bool u16 = fd.in_dtype == NRM_IN_U16_MM;
-    const int padx = pad_x(alpha, u16 ? 2 : 4);
+    const bool ok = mbar_wait_bounded(smem_u32(&full[s]), (uint32_t)((i / S) & 1), g.timeout_ns);
+    const StageInfo si = info[s];
+    const bool u16 = si.f.in_dtype == NRM_IN_U16_MM;
+    const int padx = pad_x(alpha, u16 ? 2 : 4);  // staging (TMA) box
     const int bw = TX + 2 * padx;
+    const int pad4 = pad_x(alpha, 4);             // decoded float tile
+    const int fw = TX + 2 * pad4;
     const int bh = TY + 2 * alpha;
-    const int gx0 = si.y * TX;
-    const int gy0 = si.z * TY;
-    // Decoded tiles alternate between two buffers: the barrier below (one per
-    // tile) then also guarantees that tile i - 2's buffer is no longer read.
+    const int gx0 = si.tx * TX;
+    const int gy0 = si.ty * TY;
+    // Decoded tiles alternate between two buffers: the named barrier below
+    // (one per tile) also guarantees that tile i - 2's buffer is no longer read.
     float* F = reinterpret_cast<float*>(fbase + (i & 1) * FB);
     if (ok) {
-      if (si.w) {
+      if (si.tma) {
         const unsigned char* stage = smem + (size_t)s * SB;
         if (u16)
-          decode_tile<NT>(reinterpret_cast<const uint16_t*>(stage), F, bw * bh);
+          decode_tile<NT>(reinterpret_cast<const uint16_t*>(stage), F, fw, bh, bw, padx - pad4);
         else
-          decode_tile<NT>(reinterpret_cast<const float*>(stage), F, bw * bh);
+          decode_tile<NT>(reinterpret_cast<const float*>(stage), F, fw, bh, bw, 0);
       } else {
         if (u16)
-          load_tile_decoded<uint16_t>(F, bw, bh, fd, gx0 - padx, gy0 - alpha);
+          load_tile_decoded<uint16_t, NT>(F, fw, bh, si.f, gx0 - pad4, gy0 - alpha);
         else
-          load_tile_decoded<float>(F, bw, bh, fd, gx0 - padx, gy0 - alpha);
+          load_tile_decoded<float, NT>(F, fw, bh, si.f, gx0 - pad4, gy0 - alpha);
       }
     }
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) {
-        record_error(g.status, NRM_ERR_TIMEOUT);
-        for (int j = i; j < issued; ++j)
-          mbar_wait_bounded(smem_u32(&bars[j % S]), (uint32_t)((j / S) & 1), g.timeout_ns);
-      }
+    if (bar_red_or(1, NT, !ok)) {
+      if (threadIdx.x == 0) record_error(g.status, NRM_ERR_TIMEOUT);
       return;
     }
-    // Stage s has been decoded by every thread: refill it with tile i + S.
-    if (threadIdx.x == 0 && i + S < my) issue(i + S);
-    compute_tile_any<TX, TY, NT, HALF>(F, bw, padx, tile_frame(fd, g.sign), gx0, gy0, g);
+    // Stage s and its record have been consumed by every compute thread.
+    if (threadIdx.x == 0) mbar_arrive(smem_u32(&empty[s]));
+    compute_tile_any<TX, TY, NT, HALF>(F, fw, pad4, si.f, gx0, gy0, g);
   }
 }
 

@@ -98,10 +98,10 @@ NRM_HD inline unsigned stage_bytes_for(int tile_x, int tile_y, int alpha) {
   unsigned m = f32 > u16 ? f32 : u16;
   return (m + 127) / 128 * 128;
 }
-// Bytes of the decoded float halo tile (the larger uint16 pad; f32 frames use
-// a narrower pitch inside the same buffer).
+// Bytes of the decoded float halo tile: (TX + 2 pad_x(alpha, 4)) x (TY + 2 alpha)
+// floats for either input dtype.
 NRM_HD inline unsigned ftile_bytes_for(int tile_x, int tile_y, int alpha) {
-  unsigned b = (unsigned)((tile_x + 2 * pad_x(alpha, 2)) * (tile_y + 2 * alpha) * 4);
+  unsigned b = (unsigned)((tile_x + 2 * pad_x(alpha, 4)) * (tile_y + 2 * alpha) * 4);
   return (b + 127) / 128 * 128;
 }
 // Dynamic shared memory of the plain kernel: staging buffer, decoded tile,
@@ -109,12 +109,16 @@ NRM_HD inline unsigned ftile_bytes_for(int tile_x, int tile_y, int alpha) {
 NRM_HD inline unsigned plain_smem_bytes(int tile_x, int tile_y, int alpha) {
   return stage_bytes_for(tile_x, tile_y, alpha) + ftile_bytes_for(tile_x, tile_y, alpha) + 128;
 }
+// Bytes reserved per pipeline stage for the producer's tile record.
+constexpr unsigned kStageInfoBytes = 128;
 // Dynamic shared memory of the persistent kernel: `stages` staging buffers,
-// two decoded tiles, barriers and per-stage tile info.
+// two decoded tiles, full/empty barriers (128 B) and per-stage tile records.
 NRM_HD inline unsigned persistent_smem_bytes(int tile_x, int tile_y, int alpha, int stages) {
   return stage_bytes_for(tile_x, tile_y, alpha) * stages + 2 * ftile_bytes_for(tile_x, tile_y, alpha) +
-         128 + 16 * stages;
+         128 + kStageInfoBytes * stages;
 }
+// Threads of a persistent CTA: the compute threads plus one producer warp.
+NRM_HD inline int persistent_threads(int compute_threads) { return compute_threads + 32; }
 
 // Backward (adjoint) kernel for float32 depth: output tile and threads.
 constexpr int kBwdTileX = 64;

@@ -119,6 +119,7 @@ def test_create_rejects_bad_sizes_and_intrinsics():
     assert _create(lib, H=-1)[0] == _lib.NRM_ERR_INVALID_ARG
     assert _create(lib, H=0, W=5)[0] == _lib.NRM_ERR_INVALID_ARG
     assert _create(lib, K=(0.0, 1.0, 0.0, 0.0))[0] == _lib.NRM_ERR_INVALID_ARG
+    assert _create(lib, K=(-500.0, 500.0, 0.0, 0.0))[0] == _lib.NRM_ERR_INVALID_ARG
     assert _create(lib, K=(float("inf"), 1.0, 0.0, 0.0))[0] == _lib.NRM_ERR_INVALID_ARG
     assert _create(lib, K=None)[0] == _lib.NRM_ERR_INVALID_ARG
 
