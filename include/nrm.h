@@ -182,6 +182,49 @@ NRM_API int nrm_enable_timing(nrm_handle* h, int enable);
 NRM_API int nrm_get_stats(nrm_handle* h, nrm_stats* out); /* waits for pending launches */
 NRM_API int nrm_reset_stats(nrm_handle* h);
 
+/* Largest number of frames nrm_estimate_batched_noalloc accepts per call. */
+#define NRM_NOALLOC_MAX_FRAMES 256
+
+/* The batched launch of nrm_estimate_batched for callers that cannot allocate
+ * device memory. The paper has no counterpart: this is a deployment interface,
+ * not part of the method.
+ *
+ * Who needs it: a handle allocates device memory when it is created and again
+ * when a batch outgrows its descriptor slots. Some callers must not do that:
+ * programs that reserve their whole device memory budget up front (embedded
+ * and robotics perception loops, where an allocation that fails or stalls in
+ * the middle of a run is not acceptable), and code whose device memory belongs
+ * to another allocator, such as a framework's caching allocator, which must
+ * not call cudaMalloc or cudaFree itself (cudaFree also waits for the whole
+ * device). This entry point takes no handle and allocates nothing.
+ *
+ * Frames, their buffers and the results are exactly those of
+ * nrm_estimate_batched (same per-pixel arithmetic, bit for bit) with the
+ * default launch geometry (tile 128 x 16, 256 compute threads, 3 stages).
+ * p = NULL takes the defaults; p->in_dtype is ignored (each frame has its own).
+ * device_status: a caller-owned device int, or NULL. The first device-side
+ * error of this launch (NRM_ERR_TIMEOUT) is written there; the caller zeroes it
+ * and reads it after synchronising. With NULL such an error is not reported.
+ *
+ * Scratch: the per-launch descriptors (about 65 KB for NRM_NOALLOC_MAX_FRAMES
+ * frames) live in a static device array inside this library. Every GPU that
+ * loads the library holds that array until the process exits. Every call
+ * shares it and overwrites what the previous call left there, so calls whose
+ * work overlaps on the GPU (for example on two streams, or from two threads)
+ * race; calls on one stream are ordered and safe. The host copy of the
+ * descriptors goes through cudaMemcpyAsync from pageable memory, which returns
+ * once the source has been read.
+ *
+ * The first call on a device does a one-time set-up with that device current:
+ * it looks up the array's device address (cudaGetSymbolAddress) and sets the
+ * kernel's shared-memory limit. Make that first call before any stream capture
+ * begins.
+ *
+ * Errors: NRM_ERR_UNSUPPORTED for n > NRM_NOALLOC_MAX_FRAMES (nothing is
+ * launched); otherwise as nrm_estimate_batched. */
+NRM_API int nrm_estimate_batched_noalloc(const nrm_frame* frames, int n, const nrm_params* p,
+                                         int* device_status, void* cuda_stream);
+
 NRM_API const char* nrm_status_string(int status);
 NRM_API const char* nrm_last_error(void); /* thread-local, "" if none */
 NRM_API const char* nrm_version(void);

@@ -23,6 +23,7 @@ NRM_IN_F32_M, NRM_IN_U16_MM = 0, 1
 NRM_OUT_F32X4, NRM_OUT_F16X4 = 0, 1
 NRM_MASK_RAW, NRM_MASK_SECANT = 0, 1
 NRM_MAX_ALPHA = 16
+NRM_NOALLOC_MAX_FRAMES = 256
 
 
 class Intrinsics(ctypes.Structure):
@@ -72,6 +73,8 @@ SIGNATURES = [
     ("nrm_enable_timing", ctypes.c_int, [_H, ctypes.c_int]),
     ("nrm_get_stats", ctypes.c_int, [_H, ctypes.POINTER(Stats)]),
     ("nrm_reset_stats", ctypes.c_int, [_H]),
+    ("nrm_estimate_batched_noalloc", ctypes.c_int, [ctypes.POINTER(Frame), ctypes.c_int,
+                                                    ctypes.POINTER(Params), ctypes.c_void_p, _S]),
     ("nrm_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("nrm_last_error", ctypes.c_char_p, []),
     ("nrm_version", ctypes.c_char_p, []),

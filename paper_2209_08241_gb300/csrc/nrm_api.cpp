@@ -432,6 +432,19 @@ std::string tune_key(const nrm_handle* h, const nrm_frame* f, int n) {
 
 }  // namespace
 
+namespace nrm {
+
+int host_fail(int code, const char* message) { return fail(code, "%s", message); }
+int host_validate_params(const nrm_params& p) { return validate_params(p); }
+int host_validate_frame(const nrm_frame& f, int index, int out_dtype) { return validate_frame(f, index, out_dtype); }
+void host_make_forward_desc(FrameDesc* d, const nrm_frame& f, const nrm_params& p, int tile_x, int tile_y) {
+  const int eb = f.in_dtype == NRM_IN_U16_MM ? 2 : 4;
+  make_desc(d, f.depth, f.normals, f.valid, f.H, f.W, f.depth_pitch, f.out_pitch, f.K, f.in_dtype, p, tile_x,
+            tile_y, tile_x + 2 * pad_x(p.alpha, eb), tile_y + 2 * p.alpha);
+}
+
+}  // namespace nrm
+
 // =================================================================== C ABI
 
 extern "C" {

@@ -55,11 +55,11 @@ struct BatchHeader {
 };
 static_assert(sizeof(BatchHeader) == 64, "BatchHeader layout");
 constexpr size_t kTileBeginOffset = 64;
-inline size_t frames_offset(int capacity) {
+constexpr size_t frames_offset(int capacity) {
   size_t b = kTileBeginOffset + sizeof(int) * (size_t)(capacity + 1);
   return (b + 255) / 256 * 256;
 }
-inline size_t block_bytes(int capacity) { return frames_offset(capacity) + sizeof(FrameDesc) * (size_t)capacity; }
+constexpr size_t block_bytes(int capacity) { return frames_offset(capacity) + sizeof(FrameDesc) * (size_t)capacity; }
 
 // Launch-wide parameters (by value).
 struct Globals {
@@ -119,6 +119,14 @@ NRM_HD inline unsigned persistent_smem_bytes(int tile_x, int tile_y, int alpha, 
 }
 // Threads of a persistent CTA: the compute threads plus one producer warp.
 NRM_HD inline int persistent_threads(int compute_threads) { return compute_threads + 32; }
+
+// Host helpers of the C ABI (nrm_api.cpp) shared with the other entry points:
+// validation (sets the thread-local error message) and descriptor filling for
+// the forward kernels with tile (tile_x, tile_y).
+int host_fail(int code, const char* message);
+int host_validate_params(const nrm_params& p);
+int host_validate_frame(const nrm_frame& f, int index, int out_dtype);
+void host_make_forward_desc(FrameDesc* d, const nrm_frame& f, const nrm_params& p, int tile_x, int tile_y);
 
 // Backward (adjoint) kernel for float32 depth: output tile and threads.
 constexpr int kBwdTileX = 64;
