@@ -45,7 +45,8 @@ KERNEL_SOURCES = ("paper_2209_08241_gb300/csrc/nrm_forward.cu", "paper_2209_0824
 
 # DRAM bytes per launch of the batched kernel from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only while the kernel sources hash to the key.
-NCU_TRAFFIC = {}
+# Measured on the 64 x 1080p uint16 workload (profiles/fwd_persistent_u16_64x1080p.md).
+NCU_TRAFFIC = {"dedc0456a503cd5b": 2460675584}
 
 
 def kernel_source_hash() -> str:
@@ -300,6 +301,11 @@ def bench_ours(args, dist: Dist):
         extra = bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames, dev, stream,
                              N_FRAMES)
 
+    serving = None
+    if not args.skip_serving:
+        rates = (1, 10, 100, 1000, 4000, 8000) if args.serving_full else (100, 1000, 4000, 8000)
+        serving = bench_serving(args, dev, rates, 60.0 if args.serving_full else 2.0)
+
     cpu = None
     if dist.rank == 0 and not args.skip_cpu:
         cores = cpu_cores()
@@ -325,7 +331,7 @@ def bench_ours(args, dist: Dist):
                    "l2": f"inputs larger than L2 ({px_per_step * BYTES_PER_PX / 1e6:.0f} MB moved per step)"},
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
         "clocks": clocks.summary(), "gpu_launches": args.steps,
-        "extra": extra,
+        "extra": extra, "serving": serving,
     }
     return line
 
@@ -409,8 +415,112 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
         del b, outs
     out["mixed256_mpx"] = round(mpx / 1e6, 2)
     del mix
+
+    # Differentiation: 32 x 640x480 float32 frames, forward + adjoint per frame
+    # for L = mean over valid pixels of (1 - n_hat . t).
+    Wd, Hd, Nd = 640, 480, 32
+    fr = [scenes.random_frame(4000 + i, Wd, Hd, dev, kind="f32", holes=False, clip_range=False) for i in range(Nd)]
+    tg = scenes.unit_targets(Nd, Hd, Wd, seed=4, device=dev)
+    de = nrm.NormalEstimator(fr[0][1], Hd, Wd, nrm.NormalParams(), device=dev)
+    nbuf = torch.empty((Nd, Hd, Wd, 4), device=dev)
+    vbuf = torch.empty((Nd, Hd, Wd), dtype=torch.uint8, device=dev)
+    gbuf = torch.zeros((Nd, Hd, Wd, 4), device=dev)
+    grad = torch.empty((Nd, Hd, Wd), device=dev)
+
+    def fwd_bwd():
+        for i in range(Nd):
+            de.estimate(fr[i][0], nbuf[i], vbuf[i], stream)
+        cnt = vbuf.sum(dim=(1, 2), keepdim=True).clamp(min=1).float()
+        gbuf[..., :3] = -tg * (vbuf.unsqueeze(-1).float() / cnt.unsqueeze(-1))
+        for i in range(Nd):
+            de.backward(fr[i][0], gbuf[i], vbuf[i], grad[i], stream)
+
+    for _ in range(3):
+        fwd_bwd()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        fwd_bwd()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    out["diff32_fwd_bwd_mpx_s"] = round(Nd * Hd * Wd / (ms / 1e3) / 1e6, 1)
+    e0.record(stream)
+    for _ in range(reps):
+        for i in range(Nd):
+            de.backward(fr[i][0], gbuf[i], vbuf[i], grad[i], stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    peak, _ = measured_peaks()
+    out["adjoint_mpx_s"] = round(Nd * Hd * Wd / (ms / 1e3) / 1e6, 1)
+    out["adjoint_hbm_frac"] = round(Nd * Hd * Wd * 25 / (ms / 1e3) / 1e9 / peak, 4)
+    de.sync_status()
+    del fr, tg, nbuf, vbuf, gbuf, grad
     torch.cuda.empty_cache()
     return out
+
+
+def bench_serving(args, dev, rates, seconds):
+    """Poisson arrivals of single frames (sizes from the uneven mix, float32 or
+    uint16 50/50, host memory) through the continuous-batching server and the
+    per-request plain-launch baseline; 40 GB admission budget. Also a burst of
+    requests all arriving at once (saturation throughput)."""
+    import numpy as np
+    import torch
+
+    from paper_2209_08241_gb300.serving import NormalServer, PlainServer, Request, latency_summary, run_arrivals
+    from synth import scenes
+
+    # A pool of distinct frames per (size, dtype); requests reference them.
+    pool = {}
+    for si, (W, H) in enumerate(scenes.SIZE_MIX):
+        for kind in ("f32", "u16"):
+            pool[(si, kind)] = [(lambda dk: (dk[0].cpu().pin_memory(), dk[1]))(
+                scenes.random_frame(5000 + 97 * si + 13 * j + (kind == "u16"), W, H, dev, kind=kind))
+                for j in range(2)]
+    torch.cuda.synchronize(dev)
+
+    def make_requests(n, rate, seed):
+        rng = np.random.default_rng(seed)
+        sizes = rng.choice(len(scenes.SIZE_MIX), size=n, p=np.asarray(scenes.SIZE_WEIGHTS))
+        kinds = rng.integers(0, 2, size=n)
+        offs = np.cumsum(rng.exponential(1.0 / rate, size=n)) if rate else np.zeros(n)
+        out = []
+        for i in range(n):
+            d, K = pool[(int(sizes[i]), "u16" if kinds[i] else "f32")][i % 2]
+            out.append(Request(i, d, K, t_arrival=float(offs[i])))
+        return out
+
+    res = {}
+    budget = 40 << 30
+    for rate in rates:
+        n = max(20, int(rate * seconds))
+        row = {}
+        for name, cls in (("batched", NormalServer), ("plain", PlainServer)):
+            srv = cls(budget_bytes=budget, device=dev)
+            warm = make_requests(20, 0, 1)
+            run_arrivals(srv, warm)
+            reqs = make_requests(n, rate, 2)
+            dur = run_arrivals(srv, reqs)
+            srv.sync_status()
+            row[name] = latency_summary(reqs, dur)
+            del srv
+        res[f"{rate}_fps"] = row
+    # Burst: everything arrives at t = 0.
+    n = 512
+    row = {}
+    for name, cls in (("batched", NormalServer), ("plain", PlainServer)):
+        srv = cls(budget_bytes=budget, device=dev)
+        run_arrivals(srv, make_requests(32, 0, 1))
+        reqs = make_requests(n, 0, 3)
+        dur = run_arrivals(srv, reqs)
+        srv.sync_status()
+        row[name] = latency_summary(reqs, dur)
+        del srv
+    res["burst_512"] = row
+    torch.cuda.empty_cache()
+    return res
 
 
 def bench_reference(args, dist: Dist):
@@ -473,6 +583,9 @@ def main(argv=None):
     ap.add_argument("--skip-extra", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="serving sweep at 1..8000 frames/s, 60 s each (default: 100..8000, 2 s each)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

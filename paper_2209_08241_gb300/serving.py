@@ -1,0 +1,318 @@
+"""Continuous-batching server for depth frames (the served form).
+
+Requests (one depth frame each, any size, float32 metres or uint16 units, own
+intrinsics) arrive in host memory. The server
+
+  * admits a waiting request when a device buffer set for its frame size is
+    free or can be created within the device-memory budget (buffers stay
+    resident and are reused by later requests of the same size);
+  * copies the admitted frames to the device and launches everything admitted
+    so far as ONE batched persistent launch (``nrm_estimate_batched``) on the
+    next free stream, so a batch starts while earlier batches are still on the
+    GPU and their work overlaps;
+  * retires batches as their completion events fire, hands each finished
+    request to the ``on_done`` callback (results are views of the resident
+    buffers, valid until the callback returns) and frees the buffers.
+
+Per-request latency is completion time minus arrival time, both on the host
+clock. ``PlainServer`` is the baseline: one plain per-frame launch per request,
+in arrival order, on one stream.
+
+All normal arithmetic runs in the library's CUDA kernels; this module only
+schedules, copies and keeps books.
+"""
+from __future__ import annotations
+
+import collections
+import ctypes
+import time
+from dataclasses import dataclass, field
+from typing import Callable, Optional
+
+import torch
+
+from . import BatchedEstimator, NormalEstimator, NormalParams, _lib
+
+
+@dataclass
+class Request:
+    rid: int
+    depth: torch.Tensor          # (H, W) float32 or uint16, host (pinned for async copies)
+    K: tuple                     # (fx, fy, cx, cy)
+    t_arrival: float = 0.0       # host clock (time.perf_counter)
+    t_launch: float = 0.0
+    t_done: float = 0.0
+    buffers: Optional["BufferSet"] = None
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_arrival
+
+    @property
+    def pixels(self) -> int:
+        return int(self.depth.shape[0] * self.depth.shape[1])
+
+
+@dataclass
+class BufferSet:
+    """Resident device buffers for one frame: depth in, normals and mask out."""
+    key: tuple
+    depth: torch.Tensor
+    normals: torch.Tensor
+    valid: torch.Tensor
+    nbytes: int
+
+
+class BufferPool:
+    """Device buffer sets per (H, W, depth dtype), bounded by a byte budget.
+
+    acquire() returns a free set of the right size, or creates one if the
+    budget allows, else None (the request waits). Free sets of other sizes are
+    evicted (their memory returned to the allocator) when that makes room."""
+
+    def __init__(self, budget_bytes: int, out_dtype: torch.dtype, device):
+        self.budget = int(budget_bytes)
+        self.out_dtype = out_dtype
+        self.device = device
+        self.free: dict = collections.defaultdict(list)
+        self.reserved = 0   # bytes of all sets, free or in use
+        self.in_use = 0
+
+    @staticmethod
+    def set_bytes(H: int, W: int, depth_dtype: torch.dtype, out_dtype: torch.dtype) -> int:
+        eb = 2 if depth_dtype == torch.uint16 else 4
+        ob = 16 if out_dtype == torch.float32 else 8
+        return H * W * (eb + ob + 1)
+
+    def acquire(self, H: int, W: int, depth_dtype: torch.dtype) -> Optional[BufferSet]:
+        key = (H, W, depth_dtype)
+        if self.free[key]:
+            b = self.free[key].pop()
+            self.in_use += b.nbytes
+            return b
+        need = self.set_bytes(H, W, depth_dtype, self.out_dtype)
+        if need > self.budget:
+            raise ValueError(f"a {H}x{W} frame needs {need} bytes, more than the whole budget")
+        # Evict free sets of other sizes until the new one fits.
+        while self.reserved + need > self.budget:
+            victim = next((k for k, v in self.free.items() if v), None)
+            if victim is None:
+                return None
+            b = self.free[victim].pop()
+            self.reserved -= b.nbytes
+            del b
+        b = BufferSet(key,
+                      torch.empty((H, W), dtype=depth_dtype, device=self.device),
+                      torch.empty((H, W, 4), dtype=self.out_dtype, device=self.device),
+                      torch.empty((H, W), dtype=torch.uint8, device=self.device),
+                      need)
+        self.reserved += need
+        self.in_use += need
+        return b
+
+    def release(self, b: BufferSet):
+        self.in_use -= b.nbytes
+        self.free[b.key].append(b)
+
+
+@dataclass
+class _Batch:
+    event: torch.cuda.Event
+    requests: list
+    stream_index: int
+
+
+class NormalServer:
+    """Continuous batching over ``streams`` CUDA streams (one batched handle,
+    with its own CUDA-graph slots, per stream)."""
+
+    def __init__(self, params: NormalParams | None = None, budget_bytes: int = 40 << 30,
+                 streams: int = 3, max_batch: int = 256, device=None,
+                 on_done: Callable[[Request], None] | None = None):
+        self.params = params or NormalParams()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self.pool = BufferPool(budget_bytes, self.params.torch_out_dtype, self.device)
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(streams)]
+        self.handles = [BatchedEstimator(self.params, device=self.device) for _ in range(streams)]
+        self.free_streams = list(range(streams))
+        self.max_batch = int(max_batch)
+        self.waiting: collections.deque = collections.deque()
+        self.inflight: collections.deque = collections.deque()
+        self.on_done = on_done
+        self.completed = 0
+        self.batches = 0
+        self._frames = (_lib.Frame * self.max_batch)()
+
+    def submit(self, req: Request):
+        self.waiting.append(req)
+
+    def busy(self) -> bool:
+        return bool(self.waiting or self.inflight)
+
+    def _retire(self):
+        now = None
+        while self.inflight and self.inflight[0].event.query():
+            b = self.inflight.popleft()
+            now = time.perf_counter() if now is None else now
+            for r in b.requests:
+                r.t_done = now
+                if self.on_done is not None:
+                    self.on_done(r)
+                self.pool.release(r.buffers)
+                r.buffers = None
+                self.completed += 1
+            self.free_streams.append(b.stream_index)
+
+    def _launch(self):
+        if not self.free_streams or not self.waiting:
+            return
+        batch = []
+        while self.waiting and len(batch) < self.max_batch:
+            r = self.waiting[0]
+            H, W = r.depth.shape
+            buf = self.pool.acquire(H, W, r.depth.dtype)
+            if buf is None:
+                break
+            self.waiting.popleft()
+            r.buffers = buf
+            batch.append(r)
+        if not batch:
+            return
+        si = self.free_streams.pop(0)
+        stream = self.streams[si]
+        arr = self._frames
+        t = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for i, r in enumerate(batch):
+                b = r.buffers
+                b.depth.copy_(r.depth, non_blocking=True)
+                f = arr[i]
+                f.depth = b.depth.data_ptr()
+                f.normals = b.normals.data_ptr()
+                f.valid = b.valid.data_ptr()
+                f.H, f.W = int(b.depth.shape[0]), int(b.depth.shape[1])
+                f.depth_pitch = f.W
+                f.out_pitch = f.W
+                fx, fy, cx, cy = r.K
+                f.K.fx, f.K.fy, f.K.cx, f.K.cy = float(fx), float(fy), float(cx), float(cy)
+                f.in_dtype = _lib.NRM_IN_U16_MM if b.depth.dtype == torch.uint16 else _lib.NRM_IN_F32_M
+                r.t_launch = t
+            self.handles[si].run(arr, len(batch), stream)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        self.inflight.append(_Batch(ev, batch, si))
+        self.batches += 1
+
+    def poll(self):
+        """Retire finished batches, then admit and launch what is waiting."""
+        self._retire()
+        self._launch()
+
+    def drain(self):
+        while self.busy():
+            self.poll()
+
+    def sync_status(self):
+        for h in self.handles:
+            h.sync_status()
+
+
+class PlainServer:
+    """Baseline: one plain per-frame launch per request, in arrival order, on
+    one stream, with the same resident-buffer pool."""
+
+    def __init__(self, params: NormalParams | None = None, budget_bytes: int = 40 << 30, device=None,
+                 on_done: Callable[[Request], None] | None = None):
+        self.params = params or NormalParams()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self.pool = BufferPool(budget_bytes, self.params.torch_out_dtype, self.device)
+        self.stream = torch.cuda.Stream(self.device)
+        self.estimators: dict = {}
+        self.waiting: collections.deque = collections.deque()
+        self.inflight: collections.deque = collections.deque()
+        self.on_done = on_done
+        self.completed = 0
+
+    def submit(self, req: Request):
+        self.waiting.append(req)
+
+    def busy(self) -> bool:
+        return bool(self.waiting or self.inflight)
+
+    def _estimator(self, r: Request) -> NormalEstimator:
+        H, W = r.depth.shape
+        key = (H, W, r.depth.dtype, tuple(r.K))
+        est = self.estimators.get(key)
+        if est is None:
+            est = NormalEstimator(r.K, H, W, self.params,
+                                  in_dtype="u16" if r.depth.dtype == torch.uint16 else "f32",
+                                  device=self.device)
+            self.estimators[key] = est
+        return est
+
+    def poll(self):
+        now = None
+        while self.inflight and self.inflight[0][0].query():
+            ev, r = self.inflight.popleft()
+            now = time.perf_counter() if now is None else now
+            r.t_done = now
+            if self.on_done is not None:
+                self.on_done(r)
+            self.pool.release(r.buffers)
+            r.buffers = None
+            self.completed += 1
+        while self.waiting:
+            r = self.waiting[0]
+            H, W = r.depth.shape
+            buf = self.pool.acquire(H, W, r.depth.dtype)
+            if buf is None:
+                break
+            self.waiting.popleft()
+            r.buffers = buf
+            r.t_launch = time.perf_counter()
+            with torch.cuda.stream(self.stream):
+                buf.depth.copy_(r.depth, non_blocking=True)
+                self._estimator(r).estimate(buf.depth, buf.normals, buf.valid, self.stream)
+                ev = torch.cuda.Event()
+                ev.record(self.stream)
+            self.inflight.append((ev, r))
+
+    def drain(self):
+        while self.busy():
+            self.poll()
+
+    def sync_status(self):
+        for est in self.estimators.values():
+            est.sync_status()
+
+
+def run_arrivals(server, requests: list, t0: float | None = None):
+    """Feeds requests whose ``t_arrival`` holds an offset (seconds) from t0 into
+    the server in real time, polling continuously; returns the wall duration.
+    ``t_arrival`` is rewritten to the absolute host time of the arrival."""
+    offsets = [r.t_arrival for r in requests]
+    t0 = time.perf_counter() if t0 is None else t0
+    i, n = 0, len(requests)
+    while i < n or server.busy():
+        now = time.perf_counter()
+        while i < n and t0 + offsets[i] <= now:
+            requests[i].t_arrival = t0 + offsets[i]
+            server.submit(requests[i])
+            i += 1
+        server.poll()
+    return time.perf_counter() - t0
+
+
+def latency_summary(requests: list, duration: float) -> dict:
+    lat = sorted(r.latency for r in requests)
+    n = len(lat)
+    px = sum(r.pixels for r in requests)
+
+    def pct(q):
+        return lat[min(n - 1, int(q * n))] * 1e3 if n else None
+
+    return {"requests": n, "duration_s": round(duration, 3), "mpx_s": round(px / duration / 1e6, 1) if duration else None,
+            "p50_ms": round(pct(0.50), 3) if n else None, "p99_ms": round(pct(0.99), 3) if n else None,
+            "max_ms": round(lat[-1] * 1e3, 3) if n else None}
