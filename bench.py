@@ -368,6 +368,9 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
     n16 = torch.empty((N_FRAMES, H_FULLHD, W_FULLHD, 4), dtype=torch.float16, device=dev)
     fr16, _ = h16.make_frames([(depth[i], Ks[i]) for i in range(N_FRAMES)],
                               [(n16[i], valid[i]) for i in range(N_FRAMES)])
+    if not args.no_autotune:
+        h16.autotune([(depth[i], Ks[i]) for i in range(N_FRAMES)], [(n16[i], valid[i]) for i in range(N_FRAMES)])
+    out["u16_half4_tile"] = h16.config()
     h16.enable_timing(True)
     for _ in range(5):
         h16.run(fr16, N_FRAMES, stream)
@@ -395,6 +398,9 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
         outs = [(torch.empty((*d.shape, 4), dtype=torch.float32 if od == "f32" else torch.float16, device=dev),
                  torch.empty(d.shape, dtype=torch.uint8, device=dev)) for d, _ in mix]
         fr, _ = b.make_frames(mix, outs)
+        if not args.no_autotune:
+            b.autotune(mix, outs)
+        out[f"mixed256_{od}out_tile"] = b.config()
         b.enable_timing(True)
         for _ in range(3):
             b.run(fr, len(mix), stream)
@@ -427,13 +433,17 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
     gbuf = torch.zeros((Nd, Hd, Wd, 4), device=dev)
     grad = torch.empty((Nd, Hd, Wd), device=dev)
 
+    # One batched forward launch and one batched adjoint launch per step.
+    db = nrm.BatchedEstimator(nrm.NormalParams(), device=dev)
+    items = [(fr[i][0], fr[i][1]) for i in range(Nd)]
+    dfr, _ = db.make_frames(items, [(nbuf[i], vbuf[i]) for i in range(Nd)])
+    glist, vlist, dlist = [gbuf[i] for i in range(Nd)], [vbuf[i] for i in range(Nd)], [grad[i] for i in range(Nd)]
+
     def fwd_bwd():
-        for i in range(Nd):
-            de.estimate(fr[i][0], nbuf[i], vbuf[i], stream)
+        db.run(dfr, Nd, stream)
         cnt = vbuf.sum(dim=(1, 2), keepdim=True).clamp(min=1).float()
         gbuf[..., :3] = -tg * (vbuf.unsqueeze(-1).float() / cnt.unsqueeze(-1))
-        for i in range(Nd):
-            de.backward(fr[i][0], gbuf[i], vbuf[i], grad[i], stream)
+        db.backward(items, glist, vlist, dlist, stream)
 
     for _ in range(3):
         fwd_bwd()
@@ -447,15 +457,43 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
     out["diff32_fwd_bwd_mpx_s"] = round(Nd * Hd * Wd / (ms / 1e3) / 1e6, 1)
     e0.record(stream)
     for _ in range(reps):
-        for i in range(Nd):
-            de.backward(fr[i][0], gbuf[i], vbuf[i], grad[i], stream)
+        db.backward(items, glist, vlist, dlist, stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / reps
     peak, _ = measured_peaks()
     out["adjoint_mpx_s"] = round(Nd * Hd * Wd / (ms / 1e3) / 1e6, 1)
     out["adjoint_hbm_frac"] = round(Nd * Hd * Wd * 25 / (ms / 1e3) / 1e9 / peak, 4)
+    # Per-frame adjoint launches on the same frames, for comparison.
+    e0.record(stream)
+    for _ in range(reps):
+        for i in range(Nd):
+            de.backward(fr[i][0], gbuf[i], vbuf[i], grad[i], stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    out["adjoint_per_frame_mpx_s"] = round(Nd * Hd * Wd / (ms / 1e3) / 1e6, 1)
+    # A large frame: 4096 x 3072 adjoint (the kernel's own bandwidth).
+    big, kb = scenes.random_frame(4999, 4096, 3072, dev, kind="f32", holes=False, clip_range=False)
+    be = nrm.NormalEstimator(kb, 3072, 4096, nrm.NormalParams(), device=dev)
+    bn, bv = be.estimate(big)
+    bg = torch.zeros_like(bn)
+    bg[..., 2] = bv.float()
+    bgrad = torch.empty_like(big)
+    for _ in range(3):
+        be.backward(big, bg, bv, bgrad, stream)
+    e0.record(stream)
+    for _ in range(reps):
+        be.backward(big, bg, bv, bgrad, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    out["adjoint_4096x3072_mpx_s"] = round(4096 * 3072 / (ms / 1e3) / 1e6, 1)
+    out["adjoint_4096x3072_hbm_frac"] = round(4096 * 3072 * 25 / (ms / 1e3) / 1e9 / peak, 4)
+    be.sync_status()
+    db.sync_status()
     de.sync_status()
+    del big, bn, bv, bg, bgrad
     del fr, tg, nbuf, vbuf, gbuf, grad
     torch.cuda.empty_cache()
     return out
@@ -499,20 +537,21 @@ def bench_serving(args, dev, rates, seconds):
         row = {}
         for name, cls in (("batched", NormalServer), ("plain", PlainServer)):
             srv = cls(budget_bytes=budget, device=dev)
-            warm = make_requests(20, 0, 1)
-            run_arrivals(srv, warm)
+            run_arrivals(srv, make_requests(64, 0, 1))
             reqs = make_requests(n, rate, 2)
             dur = run_arrivals(srv, reqs)
             srv.sync_status()
             row[name] = latency_summary(reqs, dur)
             del srv
         res[f"{rate}_fps"] = row
-    # Burst: everything arrives at t = 0.
+    # Burst: everything arrives at t = 0 (saturation throughput). The same
+    # burst is run once untimed first, so that both servers measure with their
+    # resident buffers already in place (no first-time allocations).
     n = 512
     row = {}
     for name, cls in (("batched", NormalServer), ("plain", PlainServer)):
         srv = cls(budget_bytes=budget, device=dev)
-        run_arrivals(srv, make_requests(32, 0, 1))
+        run_arrivals(srv, make_requests(n, 0, 3))
         reqs = make_requests(n, 0, 3)
         dur = run_arrivals(srv, reqs)
         srv.sync_status()

@@ -145,6 +145,25 @@ NRM_API int nrm_estimate_batched(nrm_handle* h, const nrm_frame* frames, int n, 
 NRM_API int nrm_backward(nrm_handle* h, const void* depth, const float* grad_normals,
                  const uint8_t* valid, float* grad_depth, void* cuda_stream);
 
+/* One frame of a batched adjoint. depth and grad_depth: H x W float32 with pitch
+ * depth_pitch elements; grad_normals (float4 per pixel, 4th component ignored)
+ * and valid (the mask the forward produced): pitch out_pitch pixels. */
+typedef struct {
+  const float* depth;
+  const float* grad_normals;
+  const uint8_t* valid;
+  float* grad_depth;
+  int H, W;
+  long long depth_pitch;
+  long long out_pitch;
+  nrm_intrinsics K;
+} nrm_grad_frame;
+
+/* nrm_backward for n float32 frames of any sizes and intrinsics in one launch
+ * over all their tiles (the handle's alpha and orientation apply). Same
+ * per-pixel arithmetic as nrm_backward. n = 0 is a no-op. */
+NRM_API int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, void* cuda_stream);
+
 /* Waits for the handle's work, returns the device status word (NRM_OK or the
  * first device-side error since the last call) and clears it. */
 NRM_API int nrm_sync_status(nrm_handle* h);

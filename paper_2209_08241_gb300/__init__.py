@@ -27,7 +27,8 @@ from ._lib import (NRM_IN_F32_M, NRM_IN_U16_MM, NRM_MASK_RAW, NRM_MASK_SECANT, N
                    NRM_OUT_F16X4, NRM_OUT_F32X4, NrmError)
 
 __all__ = ["NormalEstimator", "BatchedEstimator", "NormalParams", "NrmError", "estimate_normals",
-           "NormalsFunction", "MASK_RAW", "MASK_SECANT", "version"]
+           "estimate_normals_batch", "NormalsFunction", "NormalsBatchFunction", "MASK_RAW", "MASK_SECANT",
+           "version"]
 
 MASK_RAW = NRM_MASK_RAW
 MASK_SECANT = NRM_MASK_SECANT
@@ -276,6 +277,40 @@ class BatchedEstimator(_Handle):
             valid_host.copy_(staging["valid"], non_blocking=True)
         return staging
 
+    def backward(self, items: Sequence, grad_normals: Sequence, valids: Sequence,
+                 grad_depths: Sequence | None = None, stream=None) -> list:
+        """Adjoint of a batch in one launch: items [(depth float32 (H, W), K)],
+        grad_normals [(H, W, 4) float32], valids [(H, W) uint8 masks from the
+        forward]; returns (or fills) [(H, W) float32] depth gradients."""
+        n = len(items)
+        arr = (_lib.GradFrame * max(n, 1))()
+        outs = []
+        for i, (depth, K) in enumerate(items):
+            g, v = grad_normals[i], valids[i]
+            for t, name in ((depth, "depth"), (g, "grad_normals"), (v, "valid")):
+                _check_cuda(t, name)
+            if depth.dtype != torch.float32 or g.dtype != torch.float32:
+                raise TypeError("the adjoint needs float32 depth and float32 grad_normals")
+            H, W = depth.shape
+            gd = (torch.empty((H, W), dtype=torch.float32, device=depth.device) if grad_depths is None
+                  else grad_depths[i])
+            if tuple(g.shape) != (H, W, 4) or tuple(v.shape) != (H, W) or tuple(gd.shape) != (H, W):
+                raise ValueError("shape mismatch in the adjoint batch")
+            if depth.numel() and (depth.stride(1) != 1 or gd.stride(1) != 1 or gd.stride(0) != depth.stride(0)
+                                  or g.stride(2) != 1 or g.stride(1) != 4 or v.stride(1) != 1
+                                  or v.stride(0) * 4 != g.stride(0)):
+                raise ValueError("depth/grad_depth and grad_normals/valid must each share a row pitch")
+            f = arr[i]
+            f.depth, f.grad_normals, f.valid, f.grad_depth = (depth.data_ptr(), g.data_ptr(), v.data_ptr(),
+                                                              gd.data_ptr())
+            f.H, f.W = int(H), int(W)
+            f.depth_pitch = int(depth.stride(0)) if depth.numel() else f.W
+            f.out_pitch = int(g.stride(0) // 4) if depth.numel() else f.W
+            f.K = _intr(K)
+            outs.append(gd)
+        _lib.check(self.lib.nrm_backward_batched(self.h, arr, n, _stream_ptr(stream)), "nrm_backward_batched")
+        return outs
+
     def autotune(self, items: Sequence, outputs: Sequence | None = None, cache_path: str | None = None,
                  stream=None) -> dict:
         arr, _ = self.make_frames(items, outputs)
@@ -304,6 +339,55 @@ class NormalsFunction(torch.autograd.Function):
             return None, None
         g = grad_normals.contiguous().to(torch.float32)
         return ctx.est.backward(depth, g, valid), None
+
+
+class NormalsBatchFunction(torch.autograd.Function):
+    """Differentiable normals of a stack of float32 depth maps (B, H, W) with
+    per-frame intrinsics: forward = one nrm_estimate_batched launch, backward =
+    one nrm_backward_batched launch (masks held fixed)."""
+
+    @staticmethod
+    def forward(ctx, depth: torch.Tensor, Ks: tuple, est: "BatchedEstimator"):
+        depth = depth.contiguous()
+        B, H, W = depth.shape
+        normals = torch.empty((B, H, W, 4), dtype=est.params.torch_out_dtype, device=depth.device)
+        valid = torch.empty((B, H, W), dtype=torch.uint8, device=depth.device)
+        est([(depth[i], Ks[i]) for i in range(B)], [(normals[i], valid[i]) for i in range(B)])
+        ctx.est, ctx.Ks = est, Ks
+        ctx.save_for_backward(depth, valid)
+        ctx.mark_non_differentiable(valid)
+        return normals, valid
+
+    @staticmethod
+    def backward(ctx, grad_normals, grad_valid):
+        depth, valid = ctx.saved_tensors
+        if grad_normals is None:
+            return None, None, None
+        g = grad_normals.contiguous().to(torch.float32)
+        B = depth.shape[0]
+        grad = torch.empty_like(depth)
+        ctx.est.backward([(depth[i], ctx.Ks[i]) for i in range(B)], [g[i] for i in range(B)],
+                         [valid[i] for i in range(B)], [grad[i] for i in range(B)])
+        return grad, None, None
+
+
+_batch_estimators: dict = {}
+
+
+def estimate_normals_batch(depth: torch.Tensor, K, params: NormalParams | None = None):
+    """Differentiable (B, H, W) float32 depth -> ((B, H, W, 4) normals, (B, H, W)
+    masks). K: one (fx, fy, cx, cy) for all frames or a sequence of B of them."""
+    params = params or NormalParams()
+    B = depth.shape[0]
+    Ks = tuple(tuple(float(v) for v in k) for k in K) if len(K) == B and hasattr(K[0], "__len__") \
+        else tuple(tuple(float(v) for v in K) for _ in range(B))
+    key = (repr(params), depth.device.index)
+    est = _batch_estimators.get(key)
+    if est is None:
+        with torch.cuda.device(depth.device):
+            est = BatchedEstimator(params, device=depth.device)
+        _batch_estimators[key] = est
+    return NormalsBatchFunction.apply(depth, Ks, est)
 
 
 _estimators: dict = {}

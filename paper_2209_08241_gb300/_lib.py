@@ -44,6 +44,14 @@ class Frame(ctypes.Structure):
                 ("K", Intrinsics), ("in_dtype", ctypes.c_int)]
 
 
+class GradFrame(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_void_p), ("grad_normals", ctypes.c_void_p),
+                ("valid", ctypes.c_void_p), ("grad_depth", ctypes.c_void_p),
+                ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("depth_pitch", ctypes.c_longlong), ("out_pitch", ctypes.c_longlong),
+                ("K", Intrinsics)]
+
+
 class TileConfig(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("threads", ctypes.c_int),
                 ("stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
@@ -66,6 +74,7 @@ SIGNATURES = [
     ("nrm_estimate_batched", ctypes.c_int, [_H, ctypes.POINTER(Frame), ctypes.c_int, _S]),
     ("nrm_backward", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, _S]),
+    ("nrm_backward_batched", ctypes.c_int, [_H, ctypes.POINTER(GradFrame), ctypes.c_int, _S]),
     ("nrm_sync_status", ctypes.c_int, [_H]),
     ("nrm_get_config", ctypes.c_int, [_H, ctypes.POINTER(TileConfig)]),
     ("nrm_set_config", ctypes.c_int, [_H, ctypes.POINTER(TileConfig)]),

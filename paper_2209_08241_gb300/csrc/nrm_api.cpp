@@ -176,6 +176,15 @@ struct Slot {
   int tiles = 0;
 };
 
+// Descriptor ring slot of the batched adjoint (no graph: one plain launch).
+struct BSlot {
+  void* host = nullptr;
+  void* dev = nullptr;
+  int capacity = 0;
+  cudaEvent_t done = nullptr;
+  bool in_flight = false;
+};
+
 }  // namespace
 
 struct nrm_handle {
@@ -192,6 +201,8 @@ struct nrm_handle {
   unsigned long long timeout_ns = kDefaultTimeoutNs;
   Slot slots[kSlots];
   int next_slot = 0;
+  BSlot bslots[kSlots];
+  int next_bslot = 0;
   bool timing = false;
   nrm_stats stats = {0, 0.0, 0};
   cudaEvent_t last_single = nullptr;  // after the latest plain / backward launch
@@ -263,6 +274,10 @@ int retire_all(nrm_handle* h) {
   for (auto& s : h->slots) {
     int rc = retire_slot(h, s);
     if (rc) return rc;
+  }
+  for (auto& b : h->bslots) {
+    if (b.in_flight) NRM_CUDA(cudaEventSynchronize(b.done), "cudaEventSynchronize");
+    b.in_flight = false;
   }
   if (h->last_single) NRM_CUDA(cudaEventSynchronize(h->last_single), "cudaEventSynchronize");
   return NRM_OK;
@@ -529,6 +544,12 @@ int nrm_create(const nrm_intrinsics* K, int H, int W, const nrm_params* p, nrm_h
       return cuda_fail(e, "cudaEventCreate");
     }
   }
+  for (auto& b : h->bslots) {
+    if ((e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming)) != cudaSuccess) {
+      nrm_destroy(h);
+      return cuda_fail(e, "cudaEventCreate");
+    }
+  }
   nrm_tile_config c = {128, 16, 256, 3, 0};
   rc = configure(h, c);
   if (rc) {
@@ -552,6 +573,12 @@ void nrm_destroy(nrm_handle* h) {
     if (s.ev_start) cudaEventDestroy(s.ev_start);
     if (s.ev_end) cudaEventDestroy(s.ev_end);
     if (s.done) cudaEventDestroy(s.done);
+  }
+  for (auto& b : h->bslots) {
+    if (b.in_flight && b.done) cudaEventSynchronize(b.done);
+    if (b.host) cudaFreeHost(b.host);
+    if (b.dev) cudaFree(b.dev);
+    if (b.done) cudaEventDestroy(b.done);
   }
   if (h->last_single) {
     cudaEventSynchronize(h->last_single);
@@ -665,14 +692,93 @@ int nrm_backward(nrm_handle* h, const void* depth, const float* grad_normals, co
   DeviceGuard guard(h->device);
   FrameDesc d;
   const int p2 = nrm::pad_x(2 * h->p.alpha, 4);
-  make_desc(&d, depth, nullptr, const_cast<uint8_t*>(valid), h->H, h->W, h->W, h->W, h->K, NRM_IN_F32_M, h->p,
-            nrm::kBwdTileX, nrm::kBwdTileY, nrm::kBwdTileX + 2 * p2, nrm::kBwdTileY + 4 * h->p.alpha);
+  make_desc(&d, depth, const_cast<float*>(grad_normals), const_cast<uint8_t*>(valid), h->H, h->W, h->W, h->W,
+            h->K, NRM_IN_F32_M, h->p, nrm::kBwdTileX, nrm::kBwdTileY, nrm::kBwdTileX + 2 * p2,
+            nrm::kBwdTileY + 4 * h->p.alpha);
+  d.grad_depth = grad_depth;
   if ((h->H + nrm::kBwdTileY - 1) / nrm::kBwdTileY > 65535)
     return fail(NRM_ERR_UNSUPPORTED, "too many tile rows for the backward launch");
   nrm::Globals g = make_globals(h);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  NRM_CUDA(nrm::launch_backward(d, grad_normals, grad_depth, g, st), "launch bwd_kernel");
+  NRM_CUDA(nrm::launch_backward(d, g, st), "launch bwd_kernel");
   NRM_CUDA(cudaEventRecord(h->last_single, st), "cudaEventRecord");
+  return NRM_OK;
+}
+
+int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, void* cuda_stream) {
+  g_last_error.clear();
+  if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 0) return fail(NRM_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return NRM_OK;
+  if (!frames) return fail(NRM_ERR_INVALID_ARG, "frames is NULL");
+  const int TX = nrm::kBwdTileX, TY = nrm::kBwdTileY;
+  long long total = 0;
+  for (int i = 0; i < n; ++i) {
+    const nrm_grad_frame& f = frames[i];
+    if (f.H < 0 || f.W < 0) return fail(NRM_ERR_INVALID_ARG, "frame %d: negative size", i);
+    if ((long long)f.H * f.W == 0) continue;
+    if (!f.depth || !f.grad_normals || !f.valid || !f.grad_depth)
+      return fail(NRM_ERR_INVALID_ARG, "frame %d: NULL buffer", i);
+    if (f.depth_pitch < f.W || f.out_pitch < f.W) return fail(NRM_ERR_INVALID_ARG, "frame %d: pitch < W", i);
+    if ((uintptr_t)f.grad_normals % 16) return fail(NRM_ERR_INVALID_ARG, "frame %d: grad_normals not 16-byte aligned", i);
+    if ((uintptr_t)f.depth % 4 || (uintptr_t)f.grad_depth % 4)
+      return fail(NRM_ERR_INVALID_ARG, "frame %d: depth buffers not 4-byte aligned", i);
+    if (f.H > (1 << 24) || f.W > (1 << 24)) return fail(NRM_ERR_UNSUPPORTED, "frame %d: dimension above 2^24", i);
+    if (validate_intrinsics(f.K)) return fail(NRM_ERR_INVALID_ARG, "frame %d: bad intrinsics", i);
+    total += (long long)((f.W + TX - 1) / TX) * ((f.H + TY - 1) / TY);
+    if (total >= (1LL << 31) - 1) return fail(NRM_ERR_UNSUPPORTED, "batch exceeds 2^31 tiles");
+  }
+  if (total == 0) return NRM_OK;
+  DeviceGuard guard(h->device);
+  BSlot& s = h->bslots[h->next_bslot];
+  h->next_bslot = (h->next_bslot + 1) % kSlots;
+  if (s.in_flight) {
+    NRM_CUDA(cudaEventSynchronize(s.done), "cudaEventSynchronize");
+    s.in_flight = false;
+  }
+  if (s.capacity < n || !s.host || !s.dev) {
+    int cap = std::max(64, s.capacity);
+    while (cap < n) cap *= 2;
+    if (s.host) cudaFreeHost(s.host);
+    if (s.dev) cudaFree(s.dev);
+    s.host = s.dev = nullptr;
+    s.capacity = 0;
+    NRM_CUDA(cudaHostAlloc(&s.host, nrm::block_bytes(cap), cudaHostAllocDefault), "cudaHostAlloc");
+    NRM_CUDA(cudaMalloc(&s.dev, nrm::block_bytes(cap)), "cudaMalloc");
+    s.capacity = cap;
+  }
+  char* base = static_cast<char*>(s.host);
+  std::memset(base, 0, nrm::frames_offset(s.capacity));
+  nrm::BatchHeader* hdr = reinterpret_cast<nrm::BatchHeader*>(base);
+  int* tb = reinterpret_cast<int*>(base + nrm::kTileBeginOffset);
+  FrameDesc* fd = reinterpret_cast<FrameDesc*>(base + nrm::frames_offset(s.capacity));
+  const int p2 = nrm::pad_x(2 * h->p.alpha, 4);
+  int acc = 0;
+  for (int i = 0; i < n; ++i) {
+    const nrm_grad_frame& f = frames[i];
+    make_desc(&fd[i], f.depth, const_cast<float*>(f.grad_normals), const_cast<uint8_t*>(f.valid), f.H, f.W,
+              f.depth_pitch, f.out_pitch, f.K, NRM_IN_F32_M, h->p, TX, TY, TX + 2 * p2, TY + 4 * h->p.alpha);
+    fd[i].grad_depth = f.grad_depth;
+    fd[i].tile_begin = acc;
+    tb[i] = acc;
+    acc += fd[i].tiles_x * ((f.H + TY - 1) / TY);
+  }
+  tb[n] = acc;
+  hdr->n_frames = n;
+  hdr->total_tiles = acc;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const size_t used = nrm::frames_offset(s.capacity) + sizeof(FrameDesc) * (size_t)n;
+  NRM_CUDA(cudaMemcpyAsync(s.dev, s.host, used, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+  nrm::BatchArgs args;
+  args.hdr = reinterpret_cast<const nrm::BatchHeader*>(s.dev);
+  args.tile_begin = reinterpret_cast<const int*>(static_cast<char*>(s.dev) + nrm::kTileBeginOffset);
+  args.frames = reinterpret_cast<const FrameDesc*>(static_cast<char*>(s.dev) + nrm::frames_offset(s.capacity));
+  args.stages = 1;
+  args.stage_bytes = 0;
+  nrm::Globals g = make_globals(h);
+  NRM_CUDA(nrm::launch_backward_batched(args, acc, g, st), "launch bwd_batched_kernel");
+  NRM_CUDA(cudaEventRecord(s.done, st), "cudaEventRecord");
+  s.in_flight = true;
   return NRM_OK;
 }
 

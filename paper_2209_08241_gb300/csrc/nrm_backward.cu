@@ -16,7 +16,9 @@
 //
 // One CTA per 64 x 16 output tile: a TMA load stages the depth halo of radius
 // 2 alpha; phase 1 computes (w2, w3, w4, w5) for the tile extended by alpha into
-// shared memory; phase 2 gathers.
+// shared memory; phase 2 gathers. bwd_kernel covers one frame (grid = its
+// tiles); bwd_batched_kernel covers every tile of a batch (grid = all tiles,
+// frame found by binary search over the per-frame tile offsets).
 #include "nrm_device.cuh"
 
 namespace nrm {
@@ -39,22 +41,23 @@ __host__ __device__ inline unsigned weight_tile_bytes(int alpha) {
   return (unsigned)((TX + 2 * alpha) * (TY + 2 * alpha) * 16);
 }
 
-__global__ void __launch_bounds__(NT)
-    bwd_kernel(const __grid_constant__ FrameDesc fd, const float4* __restrict__ gn,
-               float* __restrict__ grad, const Globals g) {
-  extern __shared__ __align__(128) unsigned char smem[];
+// One output tile (gx0, gy0) of frame fd; tmap is fd's tensor map (param or
+// global memory). If the bounded wait for the TMA copy runs out, the tile
+// records NRM_ERR_TIMEOUT in the status word and writes nothing.
+__device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap, int gx0, int gy0,
+                                         const Globals& g, unsigned char* smem) {
   const int alpha = g.alpha;
   const int p2 = pad_x(2 * alpha, 4);
-  const int bw = TX + 2 * p2;      // depth tile pitch
+  const int bw = TX + 2 * p2;       // depth tile pitch
   const int bh = TY + 4 * alpha;
   const int ex_w = TX + 2 * alpha;  // weight tile pitch
   const int ex_h = TY + 2 * alpha;
   float* dep = reinterpret_cast<float*>(smem);
   float4* wts = reinterpret_cast<float4*>(smem + depth_tile_bytes(alpha));
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + depth_tile_bytes(alpha) + weight_tile_bytes(alpha));
-  const int gx0 = blockIdx.x * TX;
-  const int gy0 = blockIdx.y * TY;
   const int H = fd.H, W = fd.W;
+  const float4* __restrict__ gn = reinterpret_cast<const float4*>(fd.normals);
+  float* __restrict__ grad = fd.grad_depth;
 
   if (fd.use_tma) {
     const uint32_t b = smem_u32(bar);
@@ -65,7 +68,7 @@ __global__ void __launch_bounds__(NT)
     __syncthreads();
     if (threadIdx.x == 0) {
       mbar_arrive_expect_tx(b, (uint32_t)(bw * bh * 4));
-      tma_load_2d(smem_u32(dep), &fd.tmap, gx0 - p2, gy0 - 2 * alpha, b);
+      tma_load_2d(smem_u32(dep), tmap, gx0 - p2, gy0 - 2 * alpha, b);
     }
     const bool ok = mbar_wait_bounded(b, 0, g.timeout_ns);
     if (__syncthreads_or(!ok)) {
@@ -130,23 +133,69 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
+__global__ void __launch_bounds__(NT) bwd_kernel(const __grid_constant__ FrameDesc fd, const Globals g) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  bwd_tile(fd, &fd.tmap, blockIdx.x * TX, blockIdx.y * TY, g, smem);
+}
+
+__global__ void __launch_bounds__(NT) bwd_batched_kernel(const BatchArgs args, const Globals g) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_frame;
+  const int t = (int)blockIdx.x;
+  if (threadIdx.x == 0) {
+    // Largest frame index f with tile_begin[f] <= t (frames with no tiles are skipped).
+    int lo = 0, hi = args.hdr->n_frames - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(args.tile_begin + mid) <= t)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    s_frame = lo;
+    if (args.frames[lo].use_tma) fence_tensormap_acquire(&args.frames[lo].tmap);
+  }
+  __syncthreads();
+  const FrameDesc& fd = args.frames[s_frame];
+  const int local = t - fd.tile_begin;
+  const int ty = local / fd.tiles_x;
+  const int tx = local - ty * fd.tiles_x;
+  bwd_tile(fd, &fd.tmap, tx * TX, ty * TY, g, smem);
+}
+
+// Grants the dynamic shared memory a kernel needs, once per (kernel, device).
+cudaError_t set_smem(const void* fn, int which, unsigned bytes) {
+  static int granted[2][64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 63;
+  if ((int)bytes <= granted[which][dev]) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) granted[which][dev] = (int)bytes;
+  return e;
+}
+
 }  // namespace
 
 unsigned bwd_smem_bytes(int alpha) {
   return depth_tile_bytes(alpha) + weight_tile_bytes(alpha) + 16;
 }
 
-cudaError_t launch_backward(const FrameDesc& fd, const float* grad_normals, float* grad_depth,
-                            const Globals& g, cudaStream_t stream) {
+cudaError_t launch_backward(const FrameDesc& fd, const Globals& g, cudaStream_t stream) {
   const unsigned smem = bwd_smem_bytes(g.alpha);
-  static int configured_bytes = 0;
-  if ((int)smem > configured_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured_bytes = (int)smem;
-  }
+  cudaError_t e = set_smem((const void*)bwd_kernel, 0, smem);
+  if (e != cudaSuccess) return e;
   dim3 grid((fd.W + TX - 1) / TX, (fd.H + TY - 1) / TY);
-  bwd_kernel<<<grid, NT, smem, stream>>>(fd, reinterpret_cast<const float4*>(grad_normals), grad_depth, g);
+  bwd_kernel<<<grid, NT, smem, stream>>>(fd, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward_batched(const BatchArgs& args, int total_tiles, const Globals& g,
+                                    cudaStream_t stream) {
+  const unsigned smem = bwd_smem_bytes(g.alpha);
+  cudaError_t e = set_smem((const void*)bwd_batched_kernel, 1, smem);
+  if (e != cudaSuccess) return e;
+  bwd_batched_kernel<<<total_tiles, NT, smem, stream>>>(args, g);
   return cudaGetLastError();
 }
 

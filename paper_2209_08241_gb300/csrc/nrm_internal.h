@@ -27,8 +27,9 @@ NRM_HD inline int pad_x(int alpha, int elem_bytes) {
 struct alignas(128) FrameDesc {
   CUtensorMap tmap;        // 2-D map of the depth image, box (TX + 2 pad) x (TY + 2 alpha)
   const void* depth;
-  void* normals;
+  void* normals;           // forward: normal map; adjoint: upstream gradient (float4)
   uint8_t* valid;
+  float* grad_depth;       // adjoint only: depth gradient (pitch depth_pitch)
   long long depth_pitch;   // elements
   long long out_pitch;     // pixels (normals and mask)
   int H, W;
@@ -42,7 +43,7 @@ struct alignas(128) FrameDesc {
   int in_dtype;            // NRM_IN_F32_M or NRM_IN_U16_MM
   int use_tma;             // 1: TMA tile loads; 0: plain loads (unaligned base or pitch)
   int mask_align;          // bytes: largest power of two (<= 16) dividing mask base and pitch
-  int pad_[3];
+  int pad_;
 };
 static_assert(sizeof(FrameDesc) == 256, "FrameDesc layout");
 
@@ -133,8 +134,12 @@ constexpr int kBwdTileX = 64;
 constexpr int kBwdTileY = 16;
 constexpr int kBwdThreads = 256;
 unsigned bwd_smem_bytes(int alpha);
-// fd.tmap must map the depth with box (kBwdTileX + 2 pad_x(2 alpha, 4)) x (kBwdTileY + 4 alpha).
-cudaError_t launch_backward(const FrameDesc& fd, const float* grad_normals, float* grad_depth,
-                            const Globals& g, cudaStream_t stream);
+// fd.tmap must map the depth with box (kBwdTileX + 2 pad_x(2 alpha, 4)) x (kBwdTileY + 4 alpha);
+// fd.normals holds the upstream gradient and fd.grad_depth the output.
+cudaError_t launch_backward(const FrameDesc& fd, const Globals& g, cudaStream_t stream);
+// All tiles of a batch in one launch; the descriptor block (BatchHeader,
+// tile offsets, FrameDescs built for the adjoint) is in device memory.
+cudaError_t launch_backward_batched(const BatchArgs& args, int total_tiles, const Globals& g,
+                                    cudaStream_t stream);
 
 }  // namespace nrm
