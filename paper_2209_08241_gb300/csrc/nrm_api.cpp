@@ -94,6 +94,34 @@ bool encode_depth_map(CUtensorMap* m, const void* base, int in_dtype, int W, int
   return r == CUDA_SUCCESS;
 }
 
+// Upstream gradient of the adjoint (float4 per pixel) as a 3-D float32 tensor
+// (4, W, H); box (4, box_w, box_h) lands in shared memory as float4 per pixel.
+bool encode_grad_map(CUtensorMap* m, const void* base, int W, int H, long long out_pitch, int box_w,
+                     int box_h) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (uintptr_t)base % 16) return false;
+  cuuint64_t dims[3] = {4, (cuuint64_t)W, (cuuint64_t)H};
+  cuuint64_t strides[2] = {16, (cuuint64_t)out_pitch * 16};
+  cuuint32_t box[3] = {4, (cuuint32_t)box_w, (cuuint32_t)box_h};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The mask (one byte per pixel, pitch out_pitch) as a 2-D uint8 tensor.
+bool encode_mask_map(CUtensorMap* m, const void* base, int W, int H, long long out_pitch, int box_w, int box_h) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (uintptr_t)base % 16 || out_pitch % 16) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+  cuuint64_t strides[1] = {(cuuint64_t)out_pitch};
+  cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool finite_positive(double v) { return std::isfinite(v) && v > 0.0; }
 
 int pow2_align(uintptr_t v, int cap) {
@@ -134,6 +162,23 @@ int make_desc(FrameDesc* d, const void* depth, void* normals, uint8_t* valid, in
   if (aligned && encode_depth_map(&d->tmap, depth, in_dtype, W, H, depth_pitch, box_w, box_h)) d->use_tma = 1;
   (void)tile_y;
   return NRM_OK;
+}
+
+// Descriptor and tensor maps of one adjoint frame (float32 depth). use_tma is
+// set only when the depth, gradient and mask maps can all be made.
+void make_bwd_desc(FrameDesc* d, nrm::BwdMaps* maps, const float* depth, const float* grad_normals,
+                   const uint8_t* valid, float* grad_depth, int H, int W, long long depth_pitch,
+                   long long out_pitch, const nrm_intrinsics& K, const nrm_params& p) {
+  const int TX = nrm::kBwdTileX, TY = nrm::kBwdTileY, a = p.alpha;
+  make_desc(d, depth, const_cast<float*>(grad_normals), const_cast<uint8_t*>(valid), H, W, depth_pitch, out_pitch,
+            K, NRM_IN_F32_M, p, TX, TY, TX + 2 * nrm::pad_x(2 * a, 4), TY + 4 * a);
+  d->grad_depth = grad_depth;
+  std::memset(maps, 0, sizeof(*maps));
+  if (d->use_tma) {
+    const bool ok = encode_grad_map(&maps->grad, grad_normals, W, H, out_pitch, TX + 2 * a, TY + 2 * a) &&
+                    encode_mask_map(&maps->mask, valid, W, H, out_pitch, nrm::kBwdMaskBoxW, TY + 2 * a);
+    if (!ok) d->use_tma = 0;
+  }
 }
 
 int validate_params(const nrm_params& p) {
@@ -691,16 +736,14 @@ int nrm_backward(nrm_handle* h, const void* depth, const float* grad_normals, co
   if ((uintptr_t)depth % 4 || (uintptr_t)grad_depth % 4) return fail(NRM_ERR_INVALID_ARG, "depth not 4-byte aligned");
   DeviceGuard guard(h->device);
   FrameDesc d;
-  const int p2 = nrm::pad_x(2 * h->p.alpha, 4);
-  make_desc(&d, depth, const_cast<float*>(grad_normals), const_cast<uint8_t*>(valid), h->H, h->W, h->W, h->W,
-            h->K, NRM_IN_F32_M, h->p, nrm::kBwdTileX, nrm::kBwdTileY, nrm::kBwdTileX + 2 * p2,
-            nrm::kBwdTileY + 4 * h->p.alpha);
-  d.grad_depth = grad_depth;
+  nrm::BwdMaps maps;
+  make_bwd_desc(&d, &maps, static_cast<const float*>(depth), grad_normals, valid, grad_depth, h->H, h->W, h->W,
+                h->W, h->K, h->p);
   if ((h->H + nrm::kBwdTileY - 1) / nrm::kBwdTileY > 65535)
     return fail(NRM_ERR_UNSUPPORTED, "too many tile rows for the backward launch");
   nrm::Globals g = make_globals(h);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  NRM_CUDA(nrm::launch_backward(d, g, st), "launch bwd_kernel");
+  NRM_CUDA(nrm::launch_backward(d, maps, g, st), "launch bwd_kernel");
   NRM_CUDA(cudaEventRecord(h->last_single, st), "cudaEventRecord");
   return NRM_OK;
 }
@@ -743,8 +786,8 @@ int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, voi
     if (s.dev) cudaFree(s.dev);
     s.host = s.dev = nullptr;
     s.capacity = 0;
-    NRM_CUDA(cudaHostAlloc(&s.host, nrm::block_bytes(cap), cudaHostAllocDefault), "cudaHostAlloc");
-    NRM_CUDA(cudaMalloc(&s.dev, nrm::block_bytes(cap)), "cudaMalloc");
+    NRM_CUDA(cudaHostAlloc(&s.host, nrm::bwd_block_bytes(cap), cudaHostAllocDefault), "cudaHostAlloc");
+    NRM_CUDA(cudaMalloc(&s.dev, nrm::bwd_block_bytes(cap)), "cudaMalloc");
     s.capacity = cap;
   }
   char* base = static_cast<char*>(s.host);
@@ -752,13 +795,12 @@ int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, voi
   nrm::BatchHeader* hdr = reinterpret_cast<nrm::BatchHeader*>(base);
   int* tb = reinterpret_cast<int*>(base + nrm::kTileBeginOffset);
   FrameDesc* fd = reinterpret_cast<FrameDesc*>(base + nrm::frames_offset(s.capacity));
-  const int p2 = nrm::pad_x(2 * h->p.alpha, 4);
+  nrm::BwdMaps* maps = reinterpret_cast<nrm::BwdMaps*>(base + nrm::bwd_maps_offset(s.capacity));
   int acc = 0;
   for (int i = 0; i < n; ++i) {
     const nrm_grad_frame& f = frames[i];
-    make_desc(&fd[i], f.depth, const_cast<float*>(f.grad_normals), const_cast<uint8_t*>(f.valid), f.H, f.W,
-              f.depth_pitch, f.out_pitch, f.K, NRM_IN_F32_M, h->p, TX, TY, TX + 2 * p2, TY + 4 * h->p.alpha);
-    fd[i].grad_depth = f.grad_depth;
+    make_bwd_desc(&fd[i], &maps[i], f.depth, f.grad_normals, f.valid, f.grad_depth, f.H, f.W, f.depth_pitch,
+                  f.out_pitch, f.K, h->p);
     fd[i].tile_begin = acc;
     tb[i] = acc;
     acc += fd[i].tiles_x * ((f.H + TY - 1) / TY);
@@ -767,14 +809,14 @@ int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, voi
   hdr->n_frames = n;
   hdr->total_tiles = acc;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  const size_t used = nrm::frames_offset(s.capacity) + sizeof(FrameDesc) * (size_t)n;
+  const size_t used = nrm::bwd_maps_offset(s.capacity) + sizeof(nrm::BwdMaps) * (size_t)n;
   NRM_CUDA(cudaMemcpyAsync(s.dev, s.host, used, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
-  nrm::BatchArgs args;
-  args.hdr = reinterpret_cast<const nrm::BatchHeader*>(s.dev);
-  args.tile_begin = reinterpret_cast<const int*>(static_cast<char*>(s.dev) + nrm::kTileBeginOffset);
-  args.frames = reinterpret_cast<const FrameDesc*>(static_cast<char*>(s.dev) + nrm::frames_offset(s.capacity));
-  args.stages = 1;
-  args.stage_bytes = 0;
+  nrm::BwdBatchArgs args;
+  char* dbase = static_cast<char*>(s.dev);
+  args.hdr = reinterpret_cast<const nrm::BatchHeader*>(dbase);
+  args.tile_begin = reinterpret_cast<const int*>(dbase + nrm::kTileBeginOffset);
+  args.frames = reinterpret_cast<const FrameDesc*>(dbase + nrm::frames_offset(s.capacity));
+  args.maps = reinterpret_cast<const nrm::BwdMaps*>(dbase + nrm::bwd_maps_offset(s.capacity));
   nrm::Globals g = make_globals(h);
   NRM_CUDA(nrm::launch_backward_batched(args, acc, g, st), "launch bwd_batched_kernel");
   NRM_CUDA(cudaEventRecord(s.done, st), "cudaEventRecord");

@@ -14,11 +14,16 @@
 //   dL/dd_q = w2(q - alpha x) + w4(q + alpha x) + w3(q - alpha y) + w5(q + alpha y),
 // a deterministic gather with no atomics.
 //
-// One CTA per 64 x 16 output tile: a TMA load stages the depth halo of radius
-// 2 alpha; phase 1 computes (w2, w3, w4, w5) for the tile extended by alpha into
-// shared memory; phase 2 gathers. bwd_kernel covers one frame (grid = its
-// tiles); bwd_batched_kernel covers every tile of a batch (grid = all tiles,
-// frame found by binary search over the per-frame tile offsets).
+// One CTA per 64 x 16 output tile. Three TMA loads on one mbarrier stage the
+// tile's inputs in shared memory: the depth halo of radius 2 alpha, the upstream
+// gradient of the tile extended by alpha (a 3-D float32 box: 4 components x
+// columns x rows, i.e. float4 per pixel) and the mask of the same region (a
+// uint8 box starting 16 columns left of the tile, the alignment TMA needs).
+// Phase 1 turns each staged gradient into the four weights in place; phase 2
+// gathers. Frames whose buffers cannot be TMA-mapped use plain loads into the
+// same shared-memory layout. bwd_kernel covers one frame (grid = its tiles);
+// bwd_batched_kernel covers every tile of a batch (grid = all tiles, frame
+// found by binary search over the per-frame tile offsets).
 #include "nrm_device.cuh"
 
 namespace nrm {
@@ -30,34 +35,40 @@ namespace {
 constexpr int TX = kBwdTileX;
 constexpr int TY = kBwdTileY;
 constexpr int NT = kBwdThreads;
+constexpr int NW = NT / 32;
+constexpr int MW = kBwdMaskBoxW;   // mask tile pitch (bytes)
+constexpr int MP = kBwdMaskPad;    // mask tile column of global x = gx0 - MP
 
+__host__ __device__ inline unsigned round128(unsigned b) { return (b + 127) / 128 * 128; }
 __host__ __device__ inline unsigned depth_tile_bytes(int alpha) {
-  const int p2 = pad_x(2 * alpha, 4);
-  const unsigned b = (unsigned)((TX + 2 * p2) * (TY + 4 * alpha) * 4);
-  return (b + 127) / 128 * 128;
+  return round128((unsigned)((TX + 2 * pad_x(2 * alpha, 4)) * (TY + 4 * alpha) * 4));
 }
-
 __host__ __device__ inline unsigned weight_tile_bytes(int alpha) {
-  return (unsigned)((TX + 2 * alpha) * (TY + 2 * alpha) * 16);
+  return round128((unsigned)((TX + 2 * alpha) * (TY + 2 * alpha) * 16));
+}
+__host__ __device__ inline unsigned mask_tile_bytes(int alpha) {
+  return round128((unsigned)(MW * (TY + 2 * alpha)));
 }
 
-// One output tile (gx0, gy0) of frame fd; tmap is fd's tensor map (param or
-// global memory). If the bounded wait for the TMA copy runs out, the tile
-// records NRM_ERR_TIMEOUT in the status word and writes nothing.
-__device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap, int gx0, int gy0,
-                                         const Globals& g, unsigned char* smem) {
+// One output tile (gx0, gy0) of frame fd. tmap_d/tmap_g/tmap_m: its depth,
+// gradient and mask tensor maps (param or global memory; used only when
+// fd.use_tma). If the bounded wait for the copies runs out, the tile records
+// NRM_ERR_TIMEOUT in the status word and writes nothing.
+__device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d, const void* tmap_g,
+                                         const void* tmap_m, int gx0, int gy0, const Globals& g,
+                                         unsigned char* smem) {
   const int alpha = g.alpha;
   const int p2 = pad_x(2 * alpha, 4);
   const int bw = TX + 2 * p2;       // depth tile pitch
   const int bh = TY + 4 * alpha;
-  const int ex_w = TX + 2 * alpha;  // weight tile pitch
+  const int ex_w = TX + 2 * alpha;  // extended region (gradient / weight / mask)
   const int ex_h = TY + 2 * alpha;
   float* dep = reinterpret_cast<float*>(smem);
-  float4* wts = reinterpret_cast<float4*>(smem + depth_tile_bytes(alpha));
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + depth_tile_bytes(alpha) + weight_tile_bytes(alpha));
+  float4* gw = reinterpret_cast<float4*>(smem + depth_tile_bytes(alpha));
+  uint8_t* msk = smem + depth_tile_bytes(alpha) + weight_tile_bytes(alpha);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(msk + mask_tile_bytes(alpha));
   const int H = fd.H, W = fd.W;
-  const float4* __restrict__ gn = reinterpret_cast<const float4*>(fd.normals);
-  float* __restrict__ grad = fd.grad_depth;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   if (fd.use_tma) {
     const uint32_t b = smem_u32(bar);
@@ -67,10 +78,12 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap, 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      mbar_arrive_expect_tx(b, (uint32_t)(bw * bh * 4));
-      tma_load_2d(smem_u32(dep), tmap, gx0 - p2, gy0 - 2 * alpha, b);
+      mbar_arrive_expect_tx(b, (uint32_t)(bw * bh * 4 + ex_w * ex_h * 16 + MW * ex_h));
+      tma_load_2d(smem_u32(dep), tmap_d, gx0 - p2, gy0 - 2 * alpha, b);
+      tma_load_3d(smem_u32(gw), tmap_g, 0, gx0 - alpha, gy0 - alpha, b);
+      tma_load_2d(smem_u32(msk), tmap_m, gx0 - MP, gy0 - alpha, b);
     }
-    const bool ok = mbar_wait_bounded(b, 0, g.timeout_ns);
+    const bool ok = mbar_wait_warp(b, 0, g.timeout_ns);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         record_error(g.status, NRM_ERR_TIMEOUT);
@@ -80,29 +93,40 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap, 
     }
   } else {
     load_tile_plain(dep, bw, bh, fd, gx0 - p2, gy0 - 2 * alpha);
+    const float4* gn = reinterpret_cast<const float4*>(fd.normals);
+    for (int ey = warp; ey < ex_h; ey += NW) {
+      const int py = gy0 - alpha + ey;
+      for (int ex = lane; ex < ex_w; ex += 32) {
+        const int px = gx0 - alpha + ex;
+        const bool in = px >= 0 && py >= 0 && px < W && py < H;
+        const long long o = (long long)py * fd.out_pitch + px;
+        gw[ey * ex_w + ex] = in ? __ldg(gn + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        msk[ey * MW + ex + MP - alpha] = in ? __ldg(fd.valid + o) : (uint8_t)0;
+      }
+    }
     __syncthreads();
   }
 
+  // Phase 1: the weights of every pixel p of the extended tile, in place of
+  // its staged gradient.
   const FrameConsts k = {fd.a, fd.b, fd.c, fd.inv_fx, fd.inv_fy, fd.cx, fd.cy};
-  // Phase 1: weights of every pixel p of the extended tile.
-  for (int i = threadIdx.x; i < ex_w * ex_h; i += NT) {
-    const int ey = i / ex_w, ex = i - ey * ex_w;
-    const int px = gx0 - alpha + ex, py = gy0 - alpha + ey;
-    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (px >= 0 && py >= 0 && px < W && py < H) {
-      const long long o = (long long)py * fd.out_pitch + px;
-      if (__ldg(fd.valid + o)) {
+  for (int ey = warp; ey < ex_h; ey += NW) {
+    const int py = gy0 - alpha + ey;
+    const float v1 = ((float)py - k.cy) * k.inv_fy;
+    for (int ex = lane; ex < ex_w; ex += 32) {
+      const int px = gx0 - alpha + ex;
+      float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (msk[ey * MW + ex + MP - alpha]) {
         // p's centre in the depth tile: (px - (gx0 - p2), py - (gy0 - 2 alpha)).
         const StencilSums s = stencil_sums(dep + (ey + alpha) * bw + (ex - alpha + p2), alpha, bw);
         if (s.ok) {
           const float u1 = ((float)px - k.cx) * k.inv_fx;
-          const float v1 = ((float)py - k.cy) * k.inv_fy;
           float nx, ny, nz, P;
           closed_form_normal(s, k, u1, v1, nx, ny, nz, P);
           const float q = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
-          const float inv = rsqrtf(q);
+          const float inv = rsqrt_ftz(fmaxf(q, 1.17549435e-38f));
           const float hx0 = nx * inv, hy0 = ny * inv, hz0 = nz * inv;
-          const float4 gv = __ldg(gn + o);
+          const float4 gv = gw[ey * ex_w + ex];
           const float gd = fmaf(gv.x, hx0, fmaf(gv.y, hy0, gv.z * hz0));
           const float si = g.sign * inv;
           const float hx = (gv.x - gd * hx0) * si;
@@ -117,28 +141,32 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap, 
           w.w = -ea * s.D24 + eb * s.S24 + hc * s.S24;  // w5
         }
       }
+      gw[ey * ex_w + ex] = w;
     }
-    wts[i] = w;
   }
   __syncthreads();
   // Phase 2: gather.
-  for (int i = threadIdx.x; i < TX * TY; i += NT) {
-    const int ly = i / TX, lx = i - ly * TX;
-    const int qx = gx0 + lx, qy = gy0 + ly;
-    if (qx >= W || qy >= H) continue;
-    const int c = (ly + alpha) * ex_w + (lx + alpha);
-    const float v = wts[c - alpha].x + wts[c + alpha].z + wts[c - alpha * ex_w].y +
-                    wts[c + alpha * ex_w].w;
-    grad[(long long)qy * fd.depth_pitch + qx] = v;
+  float* __restrict__ grad = fd.grad_depth;
+  for (int ly = warp; ly < TY; ly += NW) {
+    const int qy = gy0 + ly;
+    if (qy >= H) break;
+    for (int lx = lane; lx < TX; lx += 32) {
+      const int qx = gx0 + lx;
+      if (qx >= W) break;
+      const int c = (ly + alpha) * ex_w + (lx + alpha);
+      const float v = gw[c - alpha].x + gw[c + alpha].z + gw[c - alpha * ex_w].y + gw[c + alpha * ex_w].w;
+      grad[(long long)qy * fd.depth_pitch + qx] = v;
+    }
   }
 }
 
-__global__ void __launch_bounds__(NT) bwd_kernel(const __grid_constant__ FrameDesc fd, const Globals g) {
+__global__ void __launch_bounds__(NT)
+    bwd_kernel(const __grid_constant__ FrameDesc fd, const __grid_constant__ BwdMaps maps, const Globals g) {
   extern __shared__ __align__(128) unsigned char smem[];
-  bwd_tile(fd, &fd.tmap, blockIdx.x * TX, blockIdx.y * TY, g, smem);
+  bwd_tile(fd, &fd.tmap, &maps.grad, &maps.mask, blockIdx.x * TX, blockIdx.y * TY, g, smem);
 }
 
-__global__ void __launch_bounds__(NT) bwd_batched_kernel(const BatchArgs args, const Globals g) {
+__global__ void __launch_bounds__(NT) bwd_batched_kernel(const BwdBatchArgs args, const Globals g) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_frame;
   const int t = (int)blockIdx.x;
@@ -153,14 +181,19 @@ __global__ void __launch_bounds__(NT) bwd_batched_kernel(const BatchArgs args, c
         hi = mid - 1;
     }
     s_frame = lo;
-    if (args.frames[lo].use_tma) fence_tensormap_acquire(&args.frames[lo].tmap);
+    if (args.frames[lo].use_tma) {
+      fence_tensormap_acquire(&args.frames[lo].tmap);
+      fence_tensormap_acquire(&args.maps[lo].grad);
+      fence_tensormap_acquire(&args.maps[lo].mask);
+    }
   }
   __syncthreads();
-  const FrameDesc& fd = args.frames[s_frame];
+  const int f = s_frame;
+  const FrameDesc& fd = args.frames[f];
   const int local = t - fd.tile_begin;
   const int ty = local / fd.tiles_x;
   const int tx = local - ty * fd.tiles_x;
-  bwd_tile(fd, &fd.tmap, tx * TX, ty * TY, g, smem);
+  bwd_tile(fd, &fd.tmap, &args.maps[f].grad, &args.maps[f].mask, tx * TX, ty * TY, g, smem);
 }
 
 // Grants the dynamic shared memory a kernel needs, once per (kernel, device).
@@ -178,19 +211,19 @@ cudaError_t set_smem(const void* fn, int which, unsigned bytes) {
 }  // namespace
 
 unsigned bwd_smem_bytes(int alpha) {
-  return depth_tile_bytes(alpha) + weight_tile_bytes(alpha) + 16;
+  return depth_tile_bytes(alpha) + weight_tile_bytes(alpha) + mask_tile_bytes(alpha) + 16;
 }
 
-cudaError_t launch_backward(const FrameDesc& fd, const Globals& g, cudaStream_t stream) {
+cudaError_t launch_backward(const FrameDesc& fd, const BwdMaps& maps, const Globals& g, cudaStream_t stream) {
   const unsigned smem = bwd_smem_bytes(g.alpha);
   cudaError_t e = set_smem((const void*)bwd_kernel, 0, smem);
   if (e != cudaSuccess) return e;
   dim3 grid((fd.W + TX - 1) / TX, (fd.H + TY - 1) / TY);
-  bwd_kernel<<<grid, NT, smem, stream>>>(fd, g);
+  bwd_kernel<<<grid, NT, smem, stream>>>(fd, maps, g);
   return cudaGetLastError();
 }
 
-cudaError_t launch_backward_batched(const BatchArgs& args, int total_tiles, const Globals& g,
+cudaError_t launch_backward_batched(const BwdBatchArgs& args, int total_tiles, const Globals& g,
                                     cudaStream_t stream) {
   const unsigned smem = bwd_smem_bytes(g.alpha);
   cudaError_t e = set_smem((const void*)bwd_batched_kernel, 1, smem);

@@ -77,6 +77,33 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   return false;
 }
 
+// The same wait for a whole (converged) warp: lane 0 polls, with a short sleep
+// between polls, and broadcasts the outcome; on success every lane then tests
+// the completed phase once itself, which returns at once and gives each lane
+// the acquire ordering of the barrier. A warp of waiting threads therefore
+// costs one polling thread's instructions instead of 32.
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, unsigned long long timeout_ns) {
+  const int lane = threadIdx.x & 31;
+  uint32_t ok = 0;
+  if (lane == 0) {
+    ok = mbar_try_wait(bar, parity);
+    if (!ok) {
+      const unsigned long long t0 = global_timer_ns();
+      for (uint32_t i = 0; i < (1u << 30); ++i) {
+        __nanosleep(64);
+        if (mbar_try_wait(bar, parity)) {
+          ok = 1;
+          break;
+        }
+        if (global_timer_ns() - t0 > timeout_ns) break;
+      }
+    }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (ok) ok = mbar_try_wait(bar, parity);
+  return ok != 0;
+}
+
 // 2-D tiled TMA load of box (x, y) into shared memory; completion is signalled
 // as transaction bytes on `bar`. x * element size must be a multiple of 16.
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y,
@@ -85,6 +112,16 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int 
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
       "l"(tmap), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// 3-D tiled TMA load of box (x, y, z); x * element size must be a multiple of 16.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, int x, int y, int z,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
 }
 

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(NT)
       mbar_arrive_expect_tx(b, (uint32_t)(bw * bh * eb));
       tma_load_2d(smem_u32(smem), &fd.tmap, gx0 - padx, gy0 - alpha, b);
     }
-    ok = mbar_wait_bounded(b, 0, g.timeout_ns);
+    ok = mbar_wait_warp(b, 0, g.timeout_ns);
     if (ok) {
       if (u16)
         decode_tile<NT>(reinterpret_cast<const uint16_t*>(smem), F, fw, bh, bw, padx - pad4);
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(NT + 32)
   // -------------------------------------------------------------- compute
   for (int i = 0; i < my; ++i) {
     const int s = i % S;
-    const bool ok = mbar_wait_bounded(smem_u32(&full[s]), (uint32_t)((i / S) & 1), g.timeout_ns);
+    const bool ok = mbar_wait_warp(smem_u32(&full[s]), (uint32_t)((i / S) & 1), g.timeout_ns);
     const StageInfo si = info[s];
     const bool u16 = si.f.in_dtype == NRM_IN_U16_MM;
     const int padx = pad_x(alpha, u16 ? 2 : 4);  // staging (TMA) box

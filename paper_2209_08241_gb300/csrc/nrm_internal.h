@@ -133,13 +133,37 @@ void host_make_forward_desc(FrameDesc* d, const nrm_frame& f, const nrm_params& 
 constexpr int kBwdTileX = 64;
 constexpr int kBwdTileY = 16;
 constexpr int kBwdThreads = 256;
+// Columns of the mask box to the left of the tile: the TMA box must start on a
+// 16-byte boundary, so the mask halo (alpha <= 16 columns) is read from 16.
+constexpr int kBwdMaskPad = 16;
+constexpr int kBwdMaskBoxW = kBwdTileX + 2 * kBwdMaskPad;
+
+// The adjoint's two further tensor maps per frame: the upstream gradient as a
+// 3-D float32 tensor (4, W, H), box (4, TX + 2 alpha, TY + 2 alpha), and the
+// mask as a 2-D uint8 tensor, box (kBwdMaskBoxW, TY + 2 alpha).
+struct alignas(128) BwdMaps {
+  CUtensorMap grad;
+  CUtensorMap mask;
+};
+static_assert(sizeof(BwdMaps) == 256, "BwdMaps layout");
+// Descriptor block of a batched adjoint: header, tile offsets, FrameDescs, then BwdMaps.
+constexpr size_t bwd_maps_offset(int capacity) { return frames_offset(capacity) + sizeof(FrameDesc) * (size_t)capacity; }
+constexpr size_t bwd_block_bytes(int capacity) { return bwd_maps_offset(capacity) + sizeof(BwdMaps) * (size_t)capacity; }
+
+struct BwdBatchArgs {
+  const BatchHeader* hdr;
+  const int* tile_begin;
+  const FrameDesc* frames;
+  const BwdMaps* maps;
+};
+
 unsigned bwd_smem_bytes(int alpha);
-// fd.tmap must map the depth with box (kBwdTileX + 2 pad_x(2 alpha, 4)) x (kBwdTileY + 4 alpha);
-// fd.normals holds the upstream gradient and fd.grad_depth the output.
-cudaError_t launch_backward(const FrameDesc& fd, const Globals& g, cudaStream_t stream);
-// All tiles of a batch in one launch; the descriptor block (BatchHeader,
-// tile offsets, FrameDescs built for the adjoint) is in device memory.
-cudaError_t launch_backward_batched(const BatchArgs& args, int total_tiles, const Globals& g,
+// fd.tmap maps the depth with box (kBwdTileX + 2 pad_x(2 alpha, 4)) x (kBwdTileY + 4 alpha);
+// fd.normals holds the upstream gradient, fd.valid the mask, fd.grad_depth the output.
+// fd.use_tma = 1 only if all three maps (fd.tmap, maps.grad, maps.mask) are valid.
+cudaError_t launch_backward(const FrameDesc& fd, const BwdMaps& maps, const Globals& g, cudaStream_t stream);
+// All tiles of a batch in one launch; the descriptor block is in device memory.
+cudaError_t launch_backward_batched(const BwdBatchArgs& args, int total_tiles, const Globals& g,
                                     cudaStream_t stream);
 
 }  // namespace nrm
