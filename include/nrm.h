@@ -140,7 +140,9 @@ NRM_API int nrm_estimate_batched(nrm_handle* h, const nrm_frame* frames, int n, 
  *   grad_depth[q] = sum over valid p whose stencil holds q of
  *                   g[p] . d(n_hat[p]) / d(depth[q]),
  * g = grad_normals, H x W x 4 float32 (the 4th component is ignored).
- * valid: the mask nrm_estimate produced. Deterministic (gather, no atomics).
+ * valid: the mask nrm_estimate produced for this depth (a pixel it marks valid
+ * must have a positive finite five-point stencil; other masks give undefined
+ * gradients). Deterministic (gather, no atomics).
  * Returns NRM_ERR_UNSUPPORTED for a uint16 handle. */
 NRM_API int nrm_backward(nrm_handle* h, const void* depth, const float* grad_normals,
                  const uint8_t* valid, float* grad_depth, void* cuda_stream);

@@ -754,6 +754,7 @@ int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, voi
   if (n < 0) return fail(NRM_ERR_INVALID_ARG, "n < 0");
   if (n == 0) return NRM_OK;
   if (!frames) return fail(NRM_ERR_INVALID_ARG, "frames is NULL");
+  if (n > 65535) return fail(NRM_ERR_UNSUPPORTED, "at most 65535 frames per batched adjoint");
   const int TX = nrm::kBwdTileX, TY = nrm::kBwdTileY;
   long long total = 0;
   for (int i = 0; i < n; ++i) {
@@ -818,7 +819,9 @@ int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, voi
   args.frames = reinterpret_cast<const FrameDesc*>(dbase + nrm::frames_offset(s.capacity));
   args.maps = reinterpret_cast<const nrm::BwdMaps*>(dbase + nrm::bwd_maps_offset(s.capacity));
   nrm::Globals g = make_globals(h);
-  NRM_CUDA(nrm::launch_backward_batched(args, acc, g, st), "launch bwd_batched_kernel");
+  int max_tiles = 0;
+  for (int i = 0; i < n; ++i) max_tiles = std::max(max_tiles, fd[i].tiles_x * ((frames[i].H + TY - 1) / TY));
+  NRM_CUDA(nrm::launch_backward_batched(args, n, max_tiles, g, st), "launch bwd_batched_kernel");
   NRM_CUDA(cudaEventRecord(s.done, st), "cudaEventRecord");
   s.in_flight = true;
   return NRM_OK;

@@ -22,8 +22,7 @@
 // Phase 1 turns each staged gradient into the four weights in place; phase 2
 // gathers. Frames whose buffers cannot be TMA-mapped use plain loads into the
 // same shared-memory layout. bwd_kernel covers one frame (grid = its tiles);
-// bwd_batched_kernel covers every tile of a batch (grid = all tiles, frame
-// found by binary search over the per-frame tile offsets).
+// bwd_batched_kernel covers a batch (grid = max tiles of a frame x frames).
 #include "nrm_device.cuh"
 
 namespace nrm {
@@ -108,40 +107,54 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d
   }
 
   // Phase 1: the weights of every pixel p of the extended tile, in place of
-  // its staged gradient.
+  // its staged gradient. Threads walk the ex_w x ex_h elements in row-major
+  // order with stride NT, advancing (ey, ex) by increments (no division).
+  // A pixel the forward marked valid has a positive finite five-point stencil
+  // (that is what made it valid), so only the mask is consulted here.
   const FrameConsts k = {fd.a, fd.b, fd.c, fd.inv_fx, fd.inv_fy, fd.cx, fd.cy};
-  for (int ey = warp; ey < ex_h; ey += NW) {
-    const int py = gy0 - alpha + ey;
-    const float v1 = ((float)py - k.cy) * k.inv_fy;
-    for (int ex = lane; ex < ex_w; ex += 32) {
-      const int px = gx0 - alpha + ex;
-      float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (msk[ey * MW + ex + MP - alpha]) {
-        // p's centre in the depth tile: (px - (gx0 - p2), py - (gy0 - 2 alpha)).
-        const StencilSums s = stencil_sums(dep + (ey + alpha) * bw + (ex - alpha + p2), alpha, bw);
-        if (s.ok) {
-          const float u1 = ((float)px - k.cx) * k.inv_fx;
-          float nx, ny, nz, P;
-          closed_form_normal(s, k, u1, v1, nx, ny, nz, P);
-          const float q = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
-          const float inv = rsqrt_ftz(fmaxf(q, 1.17549435e-38f));
-          const float hx0 = nx * inv, hy0 = ny * inv, hz0 = nz * inv;
-          const float4 gv = gw[ey * ex_w + ex];
-          const float gd = fmaf(gv.x, hx0, fmaf(gv.y, hy0, gv.z * hz0));
-          const float si = g.sign * inv;
-          const float hx = (gv.x - gd * hx0) * si;
-          const float hy = (gv.y - gd * hy0) * si;
-          const float hz = (gv.z - gd * hz0) * si;
-          const float ex_ = fmaf(-u1, hz, hx);
-          const float ey_ = fmaf(-v1, hz, hy);
-          const float ea = ex_ * k.a, eb = ey_ * k.b, hc = hz * k.c;
-          w.x = -ea * s.S35 - eb * s.D35 + hc * s.S35;  // w2
-          w.y = -ea * s.D24 - eb * s.S24 + hc * s.S24;  // w3
-          w.z = ea * s.S35 - eb * s.D35 + hc * s.S35;   // w4
-          w.w = -ea * s.D24 + eb * s.S24 + hc * s.S24;  // w5
-        }
-      }
-      gw[ey * ex_w + ex] = w;
+  const int n_ext = ex_w * ex_h;
+  const int step_rows = NT / ex_w, step_cols = NT - step_rows * ex_w;
+  int ey = threadIdx.x / ex_w;
+  int ex = threadIdx.x - ey * ex_w;
+  const float* dep_c = dep + alpha * bw + p2 - alpha;  // depth-tile position of (ey, ex) = (0, 0)
+  const uint8_t* msk_c = msk + MP - alpha;
+  for (int i = threadIdx.x; i < n_ext; i += NT) {
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (msk_c[ey * MW + ex]) {
+      const float* pc = dep_c + ey * bw + ex;
+      const float d2 = pc[alpha], d4 = pc[-alpha], d3 = pc[alpha * bw], d5 = pc[-alpha * bw];
+      StencilSums s;
+      s.S24 = d2 + d4;
+      s.D24 = d2 - d4;
+      s.S35 = d3 + d5;
+      s.D35 = d3 - d5;
+      const float u1 = ((float)(gx0 - alpha + ex) - k.cx) * k.inv_fx;
+      const float v1 = ((float)(gy0 - alpha + ey) - k.cy) * k.inv_fy;
+      float nx, ny, nz, P;
+      closed_form_normal(s, k, u1, v1, nx, ny, nz, P);
+      const float q = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+      const float inv = rsqrt_ftz(fmaxf(q, 1.17549435e-38f));
+      const float hx0 = nx * inv, hy0 = ny * inv, hz0 = nz * inv;
+      const float4 gv = gw[i];
+      const float gd = fmaf(gv.x, hx0, fmaf(gv.y, hy0, gv.z * hz0));
+      const float si = g.sign * inv;
+      const float hx = (gv.x - gd * hx0) * si;
+      const float hy = (gv.y - gd * hy0) * si;
+      const float hz = (gv.z - gd * hz0) * si;
+      const float ex_ = fmaf(-u1, hz, hx);
+      const float ey_ = fmaf(-v1, hz, hy);
+      const float ea = ex_ * k.a, eb = ey_ * k.b, hc = hz * k.c;
+      w.x = -ea * s.S35 - eb * s.D35 + hc * s.S35;  // w2
+      w.y = -ea * s.D24 - eb * s.S24 + hc * s.S24;  // w3
+      w.z = ea * s.S35 - eb * s.D35 + hc * s.S35;   // w4
+      w.w = -ea * s.D24 + eb * s.S24 + hc * s.S24;  // w5
+    }
+    gw[i] = w;
+    ey += step_rows;
+    ex += step_cols;
+    if (ex >= ex_w) {
+      ex -= ex_w;
+      ++ey;
     }
   }
   __syncthreads();
@@ -166,33 +179,22 @@ __global__ void __launch_bounds__(NT)
   bwd_tile(fd, &fd.tmap, &maps.grad, &maps.mask, blockIdx.x * TX, blockIdx.y * TY, g, smem);
 }
 
+// Grid (max tiles of a frame, frames): block (x, f) is tile x of frame f; frames
+// with fewer tiles leave their extra blocks idle.
 __global__ void __launch_bounds__(NT) bwd_batched_kernel(const BwdBatchArgs args, const Globals g) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ int s_frame;
-  const int t = (int)blockIdx.x;
-  if (threadIdx.x == 0) {
-    // Largest frame index f with tile_begin[f] <= t (frames with no tiles are skipped).
-    int lo = 0, hi = args.hdr->n_frames - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (__ldg(args.tile_begin + mid) <= t)
-        lo = mid;
-      else
-        hi = mid - 1;
-    }
-    s_frame = lo;
-    if (args.frames[lo].use_tma) {
-      fence_tensormap_acquire(&args.frames[lo].tmap);
-      fence_tensormap_acquire(&args.maps[lo].grad);
-      fence_tensormap_acquire(&args.maps[lo].mask);
-    }
-  }
-  __syncthreads();
-  const int f = s_frame;
+  const int f = (int)blockIdx.y;
   const FrameDesc& fd = args.frames[f];
-  const int local = t - fd.tile_begin;
-  const int ty = local / fd.tiles_x;
-  const int tx = local - ty * fd.tiles_x;
+  const int tiles_x = fd.tiles_x;
+  const int local = (int)blockIdx.x;
+  if (tiles_x == 0 || local >= tiles_x * ((fd.H + TY - 1) / TY)) return;
+  if (threadIdx.x == 0 && fd.use_tma) {
+    fence_tensormap_acquire(&fd.tmap);
+    fence_tensormap_acquire(&args.maps[f].grad);
+    fence_tensormap_acquire(&args.maps[f].mask);
+  }
+  const int ty = local / tiles_x;
+  const int tx = local - ty * tiles_x;
   bwd_tile(fd, &fd.tmap, &args.maps[f].grad, &args.maps[f].mask, tx * TX, ty * TY, g, smem);
 }
 
@@ -223,12 +225,12 @@ cudaError_t launch_backward(const FrameDesc& fd, const BwdMaps& maps, const Glob
   return cudaGetLastError();
 }
 
-cudaError_t launch_backward_batched(const BwdBatchArgs& args, int total_tiles, const Globals& g,
+cudaError_t launch_backward_batched(const BwdBatchArgs& args, int n_frames, int max_tiles, const Globals& g,
                                     cudaStream_t stream) {
   const unsigned smem = bwd_smem_bytes(g.alpha);
   cudaError_t e = set_smem((const void*)bwd_batched_kernel, 1, smem);
   if (e != cudaSuccess) return e;
-  bwd_batched_kernel<<<total_tiles, NT, smem, stream>>>(args, g);
+  bwd_batched_kernel<<<dim3(max_tiles, n_frames), NT, smem, stream>>>(args, g);
   return cudaGetLastError();
 }
 

@@ -162,8 +162,9 @@ unsigned bwd_smem_bytes(int alpha);
 // fd.normals holds the upstream gradient, fd.valid the mask, fd.grad_depth the output.
 // fd.use_tma = 1 only if all three maps (fd.tmap, maps.grad, maps.mask) are valid.
 cudaError_t launch_backward(const FrameDesc& fd, const BwdMaps& maps, const Globals& g, cudaStream_t stream);
-// All tiles of a batch in one launch; the descriptor block is in device memory.
-cudaError_t launch_backward_batched(const BwdBatchArgs& args, int total_tiles, const Globals& g,
+// All tiles of a batch in one launch (grid max_tiles x n_frames); the descriptor
+// block is in device memory.
+cudaError_t launch_backward_batched(const BwdBatchArgs& args, int n_frames, int max_tiles, const Globals& g,
                                     cudaStream_t stream);
 
 }  // namespace nrm
