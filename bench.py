@@ -390,6 +390,33 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
     h16.sync_status()
     del h16, n16
 
+    # Octahedral 2 x int16 normals on the same batch (2 + 4 + 1 = 7 B/px).
+    ho = nrm.BatchedEstimator(nrm.NormalParams(out_dtype="oct16"), device=dev)
+    no = torch.empty((N_FRAMES, H_FULLHD, W_FULLHD, 2), dtype=torch.int16, device=dev)
+    oitems = [(depth[i], Ks[i]) for i in range(N_FRAMES)]
+    oouts = [(no[i], valid[i]) for i in range(N_FRAMES)]
+    fro, _ = ho.make_frames(oitems, oouts)
+    if not args.no_autotune:
+        ho.autotune(oitems, oouts)
+    out["u16_oct16_tile"] = ho.config()
+    ho.enable_timing(True)
+    for _ in range(5):
+        ho.run(fro, N_FRAMES, stream)
+    torch.cuda.synchronize(dev)
+    ho.reset_stats()
+    e0.record(stream)
+    for _ in range(reps):
+        ho.run(fro, N_FRAMES, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    st = ho.stats()
+    kms = st["kernel_ms"] / max(1, st["launches"])
+    out["u16_oct16_mpx_s"] = round(px / (ms / 1e3) / 1e6, 1)
+    out["u16_oct16_hbm_frac"] = round(px * 7 / (kms / 1e3) / 1e9 / peak, 4)
+    ho.sync_status()
+    del ho, no
+
     # Uneven-size batch: 256 float32 frames from the size mix, one launch.
     mix = scenes.mixed_batch(256, device=dev, kind="f32")
     mpx = sum(d.numel() for d, _ in mix)

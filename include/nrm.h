@@ -76,7 +76,13 @@ typedef struct {
 } nrm_intrinsics;
 
 typedef enum { NRM_IN_F32_M = 0, NRM_IN_U16_MM = 1 } nrm_in_dtype;
-typedef enum { NRM_OUT_F32X4 = 0, NRM_OUT_F16X4 = 1 } nrm_out_dtype;
+/* Normal map encodings: 4 x float32 (x, y, z, 0), 16 B/px; 4 x IEEE half, 8 B/px;
+ * or the octahedral code of the unit normal in 2 x int16, 4 B/px (low half x,
+ * high half y; p = round(32767 q) with q = n.xy / |n|_1 folded over the diagonals
+ * where n_z < 0; decode: v = (q_x, q_y, 1 - |q_x| - |q_y|), and where v_z < 0,
+ * (v_x, v_y) = (1 - |q_y|, 1 - |q_x|) with the signs of (q_x, q_y); normalise v).
+ * Masked pixels get code 0 (the mask, not the code, says which pixels are valid). */
+typedef enum { NRM_OUT_F32X4 = 0, NRM_OUT_F16X4 = 1, NRM_OUT_OCT16 = 2 } nrm_out_dtype;
 typedef enum { NRM_MASK_RAW = 0, NRM_MASK_SECANT = 1 } nrm_mask_mode;
 
 /* Largest pixel distance alpha the kernels accept. */

@@ -24,11 +24,11 @@ import torch
 
 from . import _lib
 from ._lib import (NRM_IN_F32_M, NRM_IN_U16_MM, NRM_MASK_RAW, NRM_MASK_SECANT, NRM_MAX_ALPHA,
-                   NRM_OUT_F16X4, NRM_OUT_F32X4, NrmError)
+                   NRM_OUT_F16X4, NRM_OUT_F32X4, NRM_OUT_OCT16, NrmError)
 
 __all__ = ["NormalEstimator", "BatchedEstimator", "NormalParams", "NrmError", "estimate_normals",
            "estimate_normals_batch", "NormalsFunction", "NormalsBatchFunction", "MASK_RAW", "MASK_SECANT",
-           "version"]
+           "decode_oct16", "version"]
 
 MASK_RAW = NRM_MASK_RAW
 MASK_SECANT = NRM_MASK_SECANT
@@ -41,7 +41,7 @@ class NormalParams:
     mask_mode: str = "secant"
     tau: float = 12.0
     depth_scale: float = 0.001
-    out_dtype: str = "f32"          # "f32" (float4 per pixel) or "f16" (half4)
+    out_dtype: str = "f32"          # "f32" (float4 per pixel), "f16" (half4) or "oct16" (2 x int16)
     orient_to_camera: bool = False
 
     def to_c(self, in_dtype: int) -> _lib.Params:
@@ -51,13 +51,31 @@ class NormalParams:
         p.tau = float(self.tau)
         p.depth_scale = float(self.depth_scale)
         p.in_dtype = int(in_dtype)
-        p.out_dtype = {"f32": NRM_OUT_F32X4, "f16": NRM_OUT_F16X4}[self.out_dtype]
+        p.out_dtype = {"f32": NRM_OUT_F32X4, "f16": NRM_OUT_F16X4, "oct16": NRM_OUT_OCT16}[self.out_dtype]
         p.orient_to_camera = int(bool(self.orient_to_camera))
         return p
 
     @property
     def torch_out_dtype(self) -> torch.dtype:
-        return torch.float32 if self.out_dtype == "f32" else torch.float16
+        return {"f32": torch.float32, "f16": torch.float16, "oct16": torch.int16}[self.out_dtype]
+
+    @property
+    def out_channels(self) -> int:
+        """Elements per pixel of the normal map: 4 (x, y, z, 0) or 2 (octahedral code)."""
+        return 2 if self.out_dtype == "oct16" else 4
+
+
+def decode_oct16(codes: torch.Tensor) -> torch.Tensor:
+    """Unit normals (..., 3) float32 from octahedral codes (..., 2) int16 (the
+    NRM_OUT_OCT16 encoding). Masked pixels decode to (0, 0, 1); use the mask."""
+    q = codes.to(torch.float32) / 32767.0
+    x, y = q[..., 0], q[..., 1]
+    z = 1.0 - x.abs() - y.abs()
+    neg = z < 0
+    fx = torch.where(neg, (1.0 - y.abs()) * torch.where(x >= 0, 1.0, -1.0), x)
+    fy = torch.where(neg, (1.0 - x.abs()) * torch.where(y >= 0, 1.0, -1.0), y)
+    v = torch.stack([fx, fy, z], dim=-1)
+    return v / v.norm(dim=-1, keepdim=True)
 
 
 def version() -> str:
@@ -151,7 +169,8 @@ class NormalEstimator(_Handle):
         self.K = tuple(float(v) for v in K)
 
     def new_outputs(self):
-        n = torch.empty((self.H, self.W, 4), dtype=self.params.torch_out_dtype, device=self.device)
+        n = torch.empty((self.H, self.W, self.params.out_channels), dtype=self.params.torch_out_dtype,
+                        device=self.device)
         m = torch.empty((self.H, self.W), dtype=torch.uint8, device=self.device)
         return n, m
 
@@ -196,7 +215,7 @@ def _frame(depth: torch.Tensor, K, normals: torch.Tensor, valid: torch.Tensor) -
     f.H, f.W = int(depth.shape[0]), int(depth.shape[1])
     if depth.numel():
         f.depth_pitch = int(depth.stride(0))
-        f.out_pitch = int(normals.stride(0) // 4)
+        f.out_pitch = int(normals.stride(0) // normals.shape[2])
     else:
         f.depth_pitch = f.out_pitch = f.W
     f.K = _intr(K)
@@ -224,16 +243,17 @@ class BatchedEstimator(_Handle):
             if depth.dim() != 2 or depth.stride(1) != 1:
                 raise ValueError("each depth must be a 2-D tensor with unit column stride")
             H, W = depth.shape
+            C = self.params.out_channels
             if outputs is None:
-                nm = torch.empty((H, W, 4), dtype=self.params.torch_out_dtype, device=depth.device)
+                nm = torch.empty((H, W, C), dtype=self.params.torch_out_dtype, device=depth.device)
                 vm = torch.empty((H, W), dtype=torch.uint8, device=depth.device)
             else:
                 nm, vm = outputs[i]
-            if tuple(nm.shape) != (H, W, 4) or tuple(vm.shape) != (H, W):
-                raise ValueError("outputs must be (H, W, 4) normals and (H, W) valid")
-            if depth.numel() and (nm.stride(2) != 1 or nm.stride(1) != 4 or nm.stride(0) % 4
-                                  or vm.stride(1) != 1 or vm.stride(0) * 4 != nm.stride(0)):
-                raise ValueError("normals (H, W, 4) and valid (H, W) must share the pixel pitch")
+            if tuple(nm.shape) != (H, W, C) or tuple(vm.shape) != (H, W):
+                raise ValueError(f"outputs must be (H, W, {C}) normals and (H, W) valid")
+            if depth.numel() and (nm.stride(2) != 1 or nm.stride(1) != C or nm.stride(0) % C
+                                  or vm.stride(1) != 1 or vm.stride(0) * C != nm.stride(0)):
+                raise ValueError(f"normals (H, W, {C}) and valid (H, W) must share the pixel pitch")
             if nm.dtype != self.params.torch_out_dtype or vm.dtype != torch.uint8:
                 raise TypeError("output dtypes do not match the estimator's out_dtype / uint8")
             arr[i] = _frame(depth, K, nm, vm)

@@ -20,7 +20,7 @@ NRM_ERR_TIMEOUT = 5
 NRM_ERR_NO_DEVICE = 6
 
 NRM_IN_F32_M, NRM_IN_U16_MM = 0, 1
-NRM_OUT_F32X4, NRM_OUT_F16X4 = 0, 1
+NRM_OUT_F32X4, NRM_OUT_F16X4, NRM_OUT_OCT16 = 0, 1, 2
 NRM_MASK_RAW, NRM_MASK_SECANT = 0, 1
 NRM_MAX_ALPHA = 16
 NRM_NOALLOC_MAX_FRAMES = 256

@@ -191,7 +191,7 @@ int validate_params(const nrm_params& p) {
     return fail(NRM_ERR_INVALID_ARG, "depth_scale must be positive and finite");
   if (p.in_dtype != NRM_IN_F32_M && p.in_dtype != NRM_IN_U16_MM)
     return fail(NRM_ERR_INVALID_ARG, "in_dtype %d", p.in_dtype);
-  if (p.out_dtype != NRM_OUT_F32X4 && p.out_dtype != NRM_OUT_F16X4)
+  if (p.out_dtype != NRM_OUT_F32X4 && p.out_dtype != NRM_OUT_F16X4 && p.out_dtype != NRM_OUT_OCT16)
     return fail(NRM_ERR_INVALID_ARG, "out_dtype %d", p.out_dtype);
   if (p.orient_to_camera != 0 && p.orient_to_camera != 1)
     return fail(NRM_ERR_INVALID_ARG, "orient_to_camera must be 0 or 1");
@@ -422,7 +422,7 @@ int validate_frame(const nrm_frame& f, int i, int out_dtype) {
   if (f.depth_pitch < f.W || f.out_pitch < f.W) return fail(NRM_ERR_INVALID_ARG, "frame %d: pitch < W", i);
   if (f.in_dtype != NRM_IN_F32_M && f.in_dtype != NRM_IN_U16_MM)
     return fail(NRM_ERR_INVALID_ARG, "frame %d: in_dtype %d", i, f.in_dtype);
-  const uintptr_t na = out_dtype == NRM_OUT_F32X4 ? 16 : 8;
+  const uintptr_t na = out_dtype == NRM_OUT_F32X4 ? 16 : (out_dtype == NRM_OUT_F16X4 ? 8 : 4);
   if ((uintptr_t)f.normals % na) return fail(NRM_ERR_INVALID_ARG, "frame %d: normals not %d-byte aligned", i, (int)na);
   const int eb = f.in_dtype == NRM_IN_U16_MM ? 2 : 4;
   if ((uintptr_t)f.depth % eb) return fail(NRM_ERR_INVALID_ARG, "frame %d: depth not %d-byte aligned", i, eb);

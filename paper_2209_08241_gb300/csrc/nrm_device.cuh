@@ -321,6 +321,45 @@ __device__ __forceinline__ void load_tile_decoded(float* dst, int bw, int bh, co
 
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 
+// Hardware reciprocal, flush-to-zero (the octahedral code's quantisation step,
+// 1/32767, dwarfs its error).
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Round to the nearest integer (ties to even) for |x| < 2^22: adding 1.5 * 2^23
+// leaves the integer in the low mantissa bits.
+__device__ __forceinline__ int round_small(float x) {
+  return __float_as_int(x + 12582912.0f) - 0x4B400000;
+}
+
+// Octahedral codes of the directions of two normals (Meyer et al. 2010; Cigolle
+// et al. 2014): p = (n_x, n_y) / (|n_x| + |n_y| + |n_z|); where n_z < 0 the lower
+// half is folded over the diagonals, p <- (1 - |p_y|, 1 - |p_x|) with the signs of
+// p. Each coordinate, in [-1, 1] up to rounding, becomes the signed 16-bit integer
+// round(32767 p) (|32767 p| < 32767.5, so it fits); x in the low half of the word,
+// y in the high half. The code does not depend on the length of n.
+__device__ __forceinline__ void oct16_encode2(float2 nx, float2 ny, float2 nz, uint32_t& ca, uint32_t& cb) {
+  const float2 ax = f2(fabsf(nx.x), fabsf(nx.y)), ay = f2(fabsf(ny.x), fabsf(ny.y));
+  const float2 l1 = __fadd2_rn(__fadd2_rn(ax, ay), f2(fabsf(nz.x), fabsf(nz.y)));
+  const float2 r = f2(rcp_ftz(l1.x), rcp_ftz(l1.y));
+  const float2 px = __fmul2_rn(nx, r), py = __fmul2_rn(ny, r);
+  const float2 one = f2(1.0f, 1.0f);
+  const float2 m1 = f2(-1.0f, -1.0f);
+  const float2 rx = __ffma2_rn(m1, f2(fabsf(py.x), fabsf(py.y)), one);  // 1 - |p_y|
+  const float2 ry = __ffma2_rn(m1, f2(fabsf(px.x), fabsf(px.y)), one);  // 1 - |p_x|
+  const float qxa = nz.x < 0.0f ? copysignf(rx.x, px.x) : px.x;
+  const float qya = nz.x < 0.0f ? copysignf(ry.x, py.x) : py.x;
+  const float qxb = nz.y < 0.0f ? copysignf(rx.y, px.y) : px.y;
+  const float qyb = nz.y < 0.0f ? copysignf(ry.y, py.y) : py.y;
+  const float2 s = f2(32767.0f, 32767.0f);
+  const float2 ua = __fmul2_rn(f2(qxa, qya), s), ub = __fmul2_rn(f2(qxb, qyb), s);
+  ca = ((uint32_t)round_small(ua.x) & 0xFFFFu) | ((uint32_t)round_small(ua.y) << 16);
+  cb = ((uint32_t)round_small(ub.x) & 0xFFFFu) | ((uint32_t)round_small(ub.y) << 16);
+}
+
 // Expands the low 2 or 4 bits of b into bytes of value 0/1.
 __device__ __forceinline__ uint32_t bits_to_bytes4(uint32_t b) {
   return (b * 0x00204081u) & 0x01010101u;
@@ -335,7 +374,7 @@ __device__ __forceinline__ uint32_t bits_to_bytes4(uint32_t b) {
 // of the scalar operations. Per-column terms are computed once per tile. Mask
 // bytes are gathered with one ballot per 32 pixels and written as TX/32
 // consecutive bytes per lane.
-template <int TX, int TY, int NT, bool HALF, bool SECANT, bool FULL>
+template <int TX, int TY, int NT, int OUT, bool SECANT, bool FULL>
 __device__ __forceinline__ void compute_tile(const float* __restrict__ F, int bw, int padx,
                                              const TileFrame& f, int gx0, int gy0, int alpha,
                                              float tau2) {
@@ -405,14 +444,25 @@ __device__ __forceinline__ void compute_tile(const float* __restrict__ F, int bw
         ka = ka & (q.x <= tau2);
         kb = kb & (q.y <= tau2);
       }
+      ballots[2 * p] = __ballot_sync(0xffffffffu, ka);
+      ballots[2 * p + 1] = __ballot_sync(0xffffffffu, kb);
+      if (OUT == NRM_OUT_OCT16) {
+        // Octahedral code of n (scale-invariant: n need not be normalised).
+        uint32_t ca, cb;
+        oct16_encode2(nx, ny, nz, ca, cb);
+        ca = ka ? ca : 0u;
+        cb = kb ? cb : 0u;
+        uint32_t* dst = reinterpret_cast<uint32_t*>(f.normals) + out_row + 64 * p;
+        if (FULL || colok[2 * p]) __stcs(dst, ca);
+        if (FULL || colok[2 * p + 1]) __stcs(dst + 32, cb);
+        continue;
+      }
       const float2 inv = f2(rsqrt_ftz(q.x), rsqrt_ftz(q.y));
       const float2 ox = __fmul2_rn(nx, inv), oy = __fmul2_rn(ny, inv), oz = __fmul2_rn(nz, inv);
       // Select, not multiply: n is NaN next to invalid depths.
       const float4 va = ka ? make_float4(ox.x, oy.x, oz.x, 0.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 vb = kb ? make_float4(ox.y, oy.y, oz.y, 0.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
-      ballots[2 * p] = __ballot_sync(0xffffffffu, ka);
-      ballots[2 * p + 1] = __ballot_sync(0xffffffffu, kb);
-      if (HALF) {
+      if (OUT == NRM_OUT_F16X4) {
         const __half2 xya = __floats2half2_rn(va.x, va.y), zwa = __floats2half2_rn(va.z, 0.0f);
         const __half2 xyb = __floats2half2_rn(vb.x, vb.y), zwb = __floats2half2_rn(vb.z, 0.0f);
         uint2* dst = reinterpret_cast<uint2*>(f.normals) + out_row + 64 * p;
@@ -454,20 +504,20 @@ __device__ __forceinline__ void compute_tile(const float* __restrict__ F, int bw
 // compute_tile for the tile's mask mode, with the column checks compiled out
 // for tiles that lie entirely inside the image width (all but the last tile
 // column of a frame whose width is not a multiple of TX).
-template <int TX, int TY, int NT, bool HALF>
+template <int TX, int TY, int NT, int OUT>
 __device__ __forceinline__ void compute_tile_any(const float* __restrict__ F, int bw, int padx,
                                                  const TileFrame& f, int gx0, int gy0, const Globals& g) {
   const bool full = gx0 + TX <= f.W;
   if (g.mask_mode == NRM_MASK_SECANT) {
     if (full)
-      compute_tile<TX, TY, NT, HALF, true, true>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
+      compute_tile<TX, TY, NT, OUT, true, true>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
     else
-      compute_tile<TX, TY, NT, HALF, true, false>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
+      compute_tile<TX, TY, NT, OUT, true, false>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
   } else {
     if (full)
-      compute_tile<TX, TY, NT, HALF, false, true>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
+      compute_tile<TX, TY, NT, OUT, false, true>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
     else
-      compute_tile<TX, TY, NT, HALF, false, false>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
+      compute_tile<TX, TY, NT, OUT, false, false>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
   }
 }
 

@@ -28,7 +28,7 @@ struct alignas(16) StageInfo {
 };
 static_assert(sizeof(StageInfo) <= kStageInfoBytes, "StageInfo must fit its slot");
 
-template <int TX, int TY, int NT, bool HALF>
+template <int TX, int TY, int NT, int OUT>
 __global__ void __launch_bounds__(NT)
     fwd_plain_kernel(const __grid_constant__ FrameDesc fd, const Globals g) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -79,11 +79,11 @@ __global__ void __launch_bounds__(NT)
     }
     return;
   }
-  compute_tile_any<TX, TY, NT, HALF>(F, fw, pad4, tf, gx0, gy0, g);
+  compute_tile_any<TX, TY, NT, OUT>(F, fw, pad4, tf, gx0, gy0, g);
 }
 
 // Block = NT compute threads + one producer warp.
-template <int TX, int TY, int NT, bool HALF>
+template <int TX, int TY, int NT, int OUT>
 __global__ void __launch_bounds__(NT + 32)
     fwd_persistent_kernel(const BatchArgs args, const Globals g) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -191,16 +191,18 @@ __global__ void __launch_bounds__(NT + 32)
     }
     // Stage s and its record have been consumed by every compute thread.
     if (threadIdx.x == 0) mbar_arrive(smem_u32(&empty[s]));
-    compute_tile_any<TX, TY, NT, HALF>(F, fw, pad4, si.f, gx0, gy0, g);
+    compute_tile_any<TX, TY, NT, OUT>(F, fw, pad4, si.f, gx0, gy0, g);
   }
 }
 
 #define NRM_FWD_SET(TX, TY, NT)                                                            \
   {TX, TY, NT,                                                                             \
-   {(const void*)fwd_plain_kernel<TX, TY, NT, false>,                                      \
-    (const void*)fwd_plain_kernel<TX, TY, NT, true>},                                      \
-   {(const void*)fwd_persistent_kernel<TX, TY, NT, false>,                                 \
-    (const void*)fwd_persistent_kernel<TX, TY, NT, true>}}
+   {(const void*)fwd_plain_kernel<TX, TY, NT, NRM_OUT_F32X4>,                              \
+    (const void*)fwd_plain_kernel<TX, TY, NT, NRM_OUT_F16X4>,                              \
+    (const void*)fwd_plain_kernel<TX, TY, NT, NRM_OUT_OCT16>},                             \
+   {(const void*)fwd_persistent_kernel<TX, TY, NT, NRM_OUT_F32X4>,                         \
+    (const void*)fwd_persistent_kernel<TX, TY, NT, NRM_OUT_F16X4>,                         \
+    (const void*)fwd_persistent_kernel<TX, TY, NT, NRM_OUT_OCT16>}}
 
 // The compiled tile configurations; the first is the default. TX is at most
 // 128 so that the halo box (TX + 2 pad <= 256 elements) fits one TMA box.

@@ -83,8 +83,8 @@ struct BatchArgs {
 // A compiled forward tile configuration.
 struct FwdKernelSet {
   int tile_x, tile_y, threads;
-  const void* plain[2];       // [out_dtype] fwd_plain_kernel<...>
-  const void* persistent[2];  // [out_dtype] fwd_persistent_kernel<...>
+  const void* plain[3];       // [out_dtype] fwd_plain_kernel<...>
+  const void* persistent[3];  // [out_dtype] fwd_persistent_kernel<...>
 };
 
 // All compiled forward configurations (nrm_forward_*.cu).

@@ -58,7 +58,7 @@ int setup_device(int device, DeviceState& st) {
   if (e != cudaSuccess) return nrm::host_fail(NRM_ERR_CUDA, cudaGetErrorString(e));
   const nrm::FwdKernelSet* ks = nrm::fwd_kernel_find(kTileX, kTileY, kThreads);
   const unsigned smem_max = nrm::persistent_smem_bytes(kTileX, kTileY, NRM_MAX_ALPHA, kStages);
-  for (int out = 0; out < 2; ++out) {
+  for (int out = 0; out < 3; ++out) {
     e = cudaFuncSetAttribute(ks->persistent[out], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     if (e != cudaSuccess) return nrm::host_fail(NRM_ERR_CUDA, cudaGetErrorString(e));
   }

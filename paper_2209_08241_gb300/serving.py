@@ -81,7 +81,7 @@ class BufferPool:
     @staticmethod
     def set_bytes(H: int, W: int, depth_dtype: torch.dtype, out_dtype: torch.dtype) -> int:
         eb = 2 if depth_dtype == torch.uint16 else 4
-        ob = 16 if out_dtype == torch.float32 else 8
+        ob = {torch.float32: 16, torch.float16: 8, torch.int16: 4}[out_dtype]
         return H * W * (eb + ob + 1)
 
     def acquire(self, H: int, W: int, depth_dtype: torch.dtype) -> Optional[BufferSet]:
@@ -101,9 +101,10 @@ class BufferPool:
             b = self.free[victim].pop()
             self.reserved -= b.nbytes
             del b
+        channels = 2 if self.out_dtype == torch.int16 else 4
         b = BufferSet(key,
                       torch.empty((H, W), dtype=depth_dtype, device=self.device),
-                      torch.empty((H, W, 4), dtype=self.out_dtype, device=self.device),
+                      torch.empty((H, W, channels), dtype=self.out_dtype, device=self.device),
                       torch.empty((H, W), dtype=torch.uint8, device=self.device),
                       need)
         self.reserved += need
@@ -193,7 +194,7 @@ class NormalServer:
                 f.valid = b.valid.data_ptr()
                 f.H, f.W = int(b.depth.shape[0]), int(b.depth.shape[1])
                 f.depth_pitch = f.W
-                f.out_pitch = f.W
+                f.out_pitch = f.W  # resident buffers are dense
                 fx, fy, cx, cy = r.K
                 f.K.fx, f.K.fy, f.K.cx, f.K.cy = float(fx), float(fy), float(cx), float(cy)
                 f.in_dtype = _lib.NRM_IN_U16_MM if b.depth.dtype == torch.uint16 else _lib.NRM_IN_F32_M

@@ -104,7 +104,7 @@ def _create(lib, K=(525.0, 525.0, 319.5, 239.5), H=480, W=640, **kw):
     ({"mask_mode": 7}, _lib.NRM_ERR_INVALID_ARG),
     ({"depth_scale": 0.0}, _lib.NRM_ERR_INVALID_ARG),
     ({"in_dtype": 3}, _lib.NRM_ERR_INVALID_ARG),
-    ({"out_dtype": 2}, _lib.NRM_ERR_INVALID_ARG),
+    ({"out_dtype": 3}, _lib.NRM_ERR_INVALID_ARG),
 ])
 def test_create_rejects_bad_params(kw, code):
     lib = _lib.load()

@@ -9,7 +9,7 @@ import torch
 
 import oracle
 import paper_2209_08241_gb300 as nrm
-from parity import compare
+from parity import compare, compare_oct16, decode_oct16
 from synth import scenes
 
 pytestmark = pytest.mark.gpu
@@ -253,3 +253,40 @@ def test_autotune_picks_a_config_and_caches_it(tmp_path):
     outs = b2(frames)
     for (d, K), (n, m) in zip(frames, outs):
         compare(n, m, run_oracle(d, K, nrm.NormalParams()), 12.0, what="tuned")
+
+
+@pytest.mark.parametrize("alpha", [1, 2])
+@pytest.mark.parametrize("orient", [False, True])
+def test_oct16_output_parity(cfg1, alpha, orient):
+    """2 x int16 octahedral normals (4 B/px) against the oracle, plain and
+    batched, float32 and uint16 input."""
+    d, K = cfg1
+    p = nrm.NormalParams(alpha=alpha, out_dtype="oct16", orient_to_camera=orient)
+    n, m = plain(d, K, p)
+    assert n.dtype == torch.int16 and tuple(n.shape) == (480, 640, 2)
+    near, ang, nv = compare_oct16(n, m, run_oracle(d, K, p), p.tau, what=f"oct16 a{alpha}")
+    assert nv > 0.5 * d.numel()
+    print(f"oct16 alpha={alpha} orient={orient}: max angle {ang:.2e} rad")
+    frames = [scenes.random_frame(600 + i, W, H, DEV, kind=k)
+              for i, (W, H, k) in enumerate([(1920, 1080, "u16"), (333, 197, "f32"), (640, 480, "u16")])]
+    b = nrm.BatchedEstimator(p)
+    outs = b(frames)
+    b.sync_status()
+    for i, ((fd, fK), (fn, fm)) in enumerate(zip(frames, outs)):
+        compare_oct16(fn, fm, run_oracle(fd, fK, p), p.tau, what=f"oct16 batched #{i}")
+        pn, pm = plain(fd, fK, p)
+        assert torch.equal(pn, fn) and torch.equal(pm, fm)
+
+
+def test_oct16_decoder_round_trip_against_float_output(cfg1):
+    """The library's torch decoder and the float32 output agree within the
+    quantisation bound."""
+    d, K = cfg1
+    n32, m = plain(d, K, nrm.NormalParams())
+    n16, m16 = plain(d, K, nrm.NormalParams(out_dtype="oct16"))
+    assert torch.equal(m, m16)
+    v = m.bool()
+    dec = nrm.decode_oct16(n16)[v].double()
+    ref = n32[..., :3][v].double()
+    ang = torch.atan2(torch.linalg.cross(dec, ref).norm(dim=-1), (dec * ref).sum(-1))
+    assert float(ang.max()) <= 1e-4
