@@ -517,10 +517,36 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
     ms = e0.elapsed_time(e1) / reps
     out["adjoint_4096x3072_mpx_s"] = round(4096 * 3072 / (ms / 1e3) / 1e6, 1)
     out["adjoint_4096x3072_hbm_frac"] = round(4096 * 3072 * 25 / (ms / 1e3) / 1e9 / peak, 4)
+    # Evaluation kernels (Section 4) on the 4096 x 3072 normal map: angle
+    # images (16 + 1 in, 8 out = 25 B/px) and the MSE against itself shifted
+    # one row (2 x 17 = 34 B/px read).
+    ph = torch.empty_like(big)
+    th = torch.empty_like(big)
+    for _ in range(3):
+        nrm.spherical_images(bn, bv, stream)
+    e0.record(stream)
+    for _ in range(reps):
+        nrm.spherical_images(bn, bv, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    out["spherical_4096x3072_mpx_s"] = round(4096 * 3072 / (ms / 1e3) / 1e6, 1)
+    out["spherical_4096x3072_hbm_frac"] = round(4096 * 3072 * 25 / (ms / 1e3) / 1e9 / peak, 4)
+    ref_n, ref_v = be.estimate(torch.roll(big, 1, dims=0).contiguous())
+    for _ in range(3):
+        nrm.angle_mse(be, bn, bv, ref_n, ref_v, stream)
+    e0.record(stream)
+    for _ in range(reps):
+        nrm.angle_mse(be, bn, bv, ref_n, ref_v, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    out["angle_mse_4096x3072_mpx_s"] = round(4096 * 3072 / (ms / 1e3) / 1e6, 1)
+    out["angle_mse_4096x3072_hbm_frac"] = round(4096 * 3072 * 34 / (ms / 1e3) / 1e9 / peak, 4)
     be.sync_status()
     db.sync_status()
     de.sync_status()
-    del big, bn, bv, bg, bgrad
+    del big, bn, bv, bg, bgrad, ph, th, ref_n, ref_v
     del fr, tg, nbuf, vbuf, gbuf, grad
     torch.cuda.empty_cache()
     return out

@@ -172,6 +172,24 @@ typedef struct {
  * per-pixel arithmetic as nrm_backward. n = 0 is a no-op. */
 NRM_API int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, void* cuda_stream);
 
+/* Spherical angle images of a normal map (Section 4, the I_phi and I_theta
+ * images, normalised to [0, 2 pi]): for each valid pixel
+ *   phi = atan2(n_y, n_x) in [0, 2 pi),  theta = atan2(sqrt(n_x^2 + n_y^2), n_z) in [0, pi];
+ * masked pixels get 0. normals: H x W x 4 float32; valid: H x W bytes; phi and
+ * theta: H x W float32; one pitch (pixels) for all four. Device pointers;
+ * asynchronous on the stream. */
+NRM_API int nrm_spherical(const float* normals, const uint8_t* valid, int H, int W, long long pitch, float* phi,
+                          float* theta, void* cuda_stream);
+
+/* Mean squared error of the angle images (Section 4, Tables 2-5) between an
+ * estimate and a reference normal map, over the pixels valid in both, with
+ * plain differences of the [0, 2 pi) values. out: 3 doubles in device memory,
+ * {MSE of I_theta, MSE of I_phi, number of pixels}. Deterministic: a fixed
+ * reduction order, no atomics. Uses scratch owned by the handle (allocated on
+ * the first call); calls on one handle must not overlap on the GPU. */
+NRM_API int nrm_angle_mse(nrm_handle* h, const float* normals, const uint8_t* valid, const float* ref_normals,
+                          const uint8_t* ref_valid, int H, int W, long long pitch, double* out, void* cuda_stream);
+
 /* Waits for the handle's work, returns the device status word (NRM_OK or the
  * first device-side error since the last call) and clears it. */
 NRM_API int nrm_sync_status(nrm_handle* h);

@@ -28,7 +28,7 @@ from ._lib import (NRM_IN_F32_M, NRM_IN_U16_MM, NRM_MASK_RAW, NRM_MASK_SECANT, N
 
 __all__ = ["NormalEstimator", "BatchedEstimator", "NormalParams", "NrmError", "estimate_normals",
            "estimate_normals_batch", "NormalsFunction", "NormalsBatchFunction", "MASK_RAW", "MASK_SECANT",
-           "decode_oct16", "version"]
+           "decode_oct16", "spherical_images", "angle_mse", "version"]
 
 MASK_RAW = NRM_MASK_RAW
 MASK_SECANT = NRM_MASK_SECANT
@@ -389,6 +389,47 @@ class NormalsBatchFunction(torch.autograd.Function):
         ctx.est.backward([(depth[i], ctx.Ks[i]) for i in range(B)], [g[i] for i in range(B)],
                          [valid[i] for i in range(B)], [grad[i] for i in range(B)])
         return grad, None, None
+
+
+def _check_map(n: torch.Tensor, v: torch.Tensor, name: str):
+    _check_cuda(n, name)
+    _check_cuda(v, name + " mask")
+    if n.dtype != torch.float32 or n.dim() != 3 or n.shape[2] != 4 or v.dtype != torch.uint8:
+        raise TypeError(f"{name}: expected (H, W, 4) float32 normals and an (H, W) uint8 mask")
+    if tuple(v.shape) != tuple(n.shape[:2]) or n.stride(2) != 1 or n.stride(1) != 4 or v.stride(1) != 1 \
+            or v.stride(0) * 4 != n.stride(0):
+        raise ValueError(f"{name}: normals and mask must share one pixel pitch")
+
+
+def spherical_images(normals: torch.Tensor, valid: torch.Tensor, stream=None):
+    """(phi, theta) images (Section 4: I_phi in [0, 2 pi), I_theta in [0, pi]) of a
+    float4 normal map; masked pixels get 0."""
+    _check_map(normals, valid, "normals")
+    H, W = valid.shape
+    phi = torch.empty((H, W), dtype=torch.float32, device=normals.device)
+    theta = torch.empty_like(phi)
+    if H * W:
+        if phi.stride(0) != valid.stride(0):
+            raise ValueError("dense (H, W) outputs need a dense mask")
+        _lib.check(_lib.load().nrm_spherical(normals.data_ptr(), valid.data_ptr(), H, W, valid.stride(0),
+                                             phi.data_ptr(), theta.data_ptr(), _stream_ptr(stream)),
+                   "nrm_spherical")
+    return phi, theta
+
+
+def angle_mse(est, normals, valid, ref_normals, ref_valid, stream=None) -> torch.Tensor:
+    """(MSE of I_theta, MSE of I_phi, count) as a float64 CUDA tensor of 3, over
+    the pixels valid in both maps (Tables 2-5); ``est`` provides the scratch."""
+    _check_map(normals, valid, "normals")
+    _check_map(ref_normals, ref_valid, "ref_normals")
+    if valid.shape != ref_valid.shape or valid.stride(0) != ref_valid.stride(0):
+        raise ValueError("the two maps must have one shape and pitch")
+    out = torch.zeros(3, dtype=torch.float64, device=normals.device)
+    H, W = valid.shape
+    _lib.check(est.lib.nrm_angle_mse(est.h, normals.data_ptr(), valid.data_ptr(), ref_normals.data_ptr(),
+                                     ref_valid.data_ptr(), H, W, valid.stride(0), out.data_ptr(),
+                                     _stream_ptr(stream)), "nrm_angle_mse")
+    return out
 
 
 _batch_estimators: dict = {}

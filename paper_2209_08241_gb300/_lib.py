@@ -75,6 +75,10 @@ SIGNATURES = [
     ("nrm_backward", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, _S]),
     ("nrm_backward_batched", ctypes.c_int, [_H, ctypes.POINTER(GradFrame), ctypes.c_int, _S]),
+    ("nrm_spherical", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, _S]),
+    ("nrm_angle_mse", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, _S]),
     ("nrm_sync_status", ctypes.c_int, [_H]),
     ("nrm_get_config", ctypes.c_int, [_H, ctypes.POINTER(TileConfig)]),
     ("nrm_set_config", ctypes.c_int, [_H, ctypes.POINTER(TileConfig)]),

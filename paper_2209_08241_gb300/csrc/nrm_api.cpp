@@ -251,6 +251,7 @@ struct nrm_handle {
   bool timing = false;
   nrm_stats stats = {0, 0.0, 0};
   cudaEvent_t last_single = nullptr;  // after the latest plain / backward launch
+  double* d_mse_partials = nullptr;   // nrm_angle_mse scratch (3 kMseBlocks doubles)
   std::vector<FrameDesc> scratch_desc;
 };
 
@@ -630,6 +631,7 @@ void nrm_destroy(nrm_handle* h) {
     cudaEventDestroy(h->last_single);
   }
   if (h->d_status) cudaFree(h->d_status);
+  if (h->d_mse_partials) cudaFree(h->d_mse_partials);
   delete h;
 }
 
@@ -824,6 +826,47 @@ int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, voi
   NRM_CUDA(nrm::launch_backward_batched(args, n, max_tiles, g, st), "launch bwd_batched_kernel");
   NRM_CUDA(cudaEventRecord(s.done, st), "cudaEventRecord");
   s.in_flight = true;
+  return NRM_OK;
+}
+
+static int check_eval_args(const float* n, const uint8_t* v, int H, int W, long long pitch) {
+  if (H < 0 || W < 0) return fail(NRM_ERR_INVALID_ARG, "negative size");
+  if ((long long)H * W == 0) return NRM_OK;
+  if (!n || !v) return fail(NRM_ERR_INVALID_ARG, "NULL buffer");
+  if (pitch < W) return fail(NRM_ERR_INVALID_ARG, "pitch < W");
+  if ((uintptr_t)n % 16) return fail(NRM_ERR_INVALID_ARG, "normals not 16-byte aligned");
+  return NRM_OK;
+}
+
+int nrm_spherical(const float* normals, const uint8_t* valid, int H, int W, long long pitch, float* phi,
+                  float* theta, void* cuda_stream) {
+  g_last_error.clear();
+  int rc = check_eval_args(normals, valid, H, W, pitch);
+  if (rc) return rc;
+  if ((long long)H * W == 0) return NRM_OK;
+  if (!phi || !theta) return fail(NRM_ERR_INVALID_ARG, "NULL output");
+  if ((uintptr_t)phi % 4 || (uintptr_t)theta % 4) return fail(NRM_ERR_INVALID_ARG, "outputs not 4-byte aligned");
+  NRM_CUDA(nrm::launch_spherical(normals, valid, H, W, pitch, phi, theta, static_cast<cudaStream_t>(cuda_stream)),
+           "launch spherical_kernel");
+  return NRM_OK;
+}
+
+int nrm_angle_mse(nrm_handle* h, const float* normals, const uint8_t* valid, const float* ref_normals,
+                  const uint8_t* ref_valid, int H, int W, long long pitch, double* out, void* cuda_stream) {
+  g_last_error.clear();
+  if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
+  if (!out || (uintptr_t)out % 8) return fail(NRM_ERR_INVALID_ARG, "out must be 8-byte aligned device memory");
+  int rc = check_eval_args(normals, valid, H, W, pitch);
+  if (rc) return rc;
+  rc = check_eval_args(ref_normals, ref_valid, H, W, pitch);
+  if (rc) return rc;
+  DeviceGuard guard(h->device);
+  if (!h->d_mse_partials)
+    NRM_CUDA(cudaMalloc(&h->d_mse_partials, sizeof(double) * 3 * nrm::kMseBlocks), "cudaMalloc");
+  NRM_CUDA(nrm::launch_angle_mse(normals, valid, ref_normals, ref_valid, H, W, pitch, h->d_mse_partials, out,
+                                 static_cast<cudaStream_t>(cuda_stream)),
+           "launch mse kernels");
+  NRM_CUDA(cudaEventRecord(h->last_single, static_cast<cudaStream_t>(cuda_stream)), "cudaEventRecord");
   return NRM_OK;
 }
 

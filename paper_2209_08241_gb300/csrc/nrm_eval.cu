@@ -1,0 +1,141 @@
+// Evaluation kernels (arXiv 2209.08241, Section 4): the spherical angle images
+// I_phi, I_theta of a normal map and the mean squared error of those images
+// between an estimate and a reference (Tables 2-5).
+//
+//   phi   = atan2(n_y, n_x), taken into [0, 2 pi)
+//   theta = atan2(sqrt(n_x^2 + n_y^2), n_z), in [0, pi]
+//
+// over valid pixels (masked pixels get 0). The MSE is the mean, over pixels
+// valid in both maps, of the squared plain differences of the angle images.
+// It is reduced deterministically: a fixed grid of kMseBlocks blocks, each
+// summing a fixed set of rows (per thread in FP32, across the block in FP64)
+// in a fixed order, then one block summing the partials in a fixed order. No
+// atomics.
+#include "nrm_device.cuh"
+
+namespace nrm {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void angles(float4 n, float& phi, float& theta) {
+  phi = atan2f(n.y, n.x);
+  phi = phi < 0.0f ? phi + 6.28318530717958647692f : phi;
+  theta = atan2f(sqrtf(fmaf(n.x, n.x, n.y * n.y)), n.z);
+}
+
+__global__ void __launch_bounds__(kThreads)
+    spherical_kernel(const float4* __restrict__ n, const uint8_t* __restrict__ valid, int H, int W,
+                     long long pitch, float* __restrict__ phi, float* __restrict__ theta) {
+  const int x = blockIdx.x * kThreads + threadIdx.x;
+  if (x >= W) return;
+  for (int y = blockIdx.y; y < H; y += gridDim.y) {
+    const long long o = (long long)y * pitch + x;
+    float p = 0.0f, t = 0.0f;
+    if (__ldg(valid + o)) angles(__ldg(n + o), p, t);
+    __stcs(phi + o, p);
+    __stcs(theta + o, t);
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Sums three values over the block in a fixed order; thread 0 gets the totals.
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
+  __shared__ double s[3][kThreads / 32];
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s[0][warp] = a;
+    s[1][warp] = b;
+    s[2][warp] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = b = c = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      a += s[0][w];
+      b += s[1][w];
+      c += s[2][w];
+    }
+  }
+}
+
+// Block b sums rows b, b + gridDim.x, ...; partials[3 b + {0,1,2}] =
+// (sum of dtheta^2, sum of dphi^2, count).
+__global__ void __launch_bounds__(kThreads)
+    mse_partial_kernel(const float4* __restrict__ na, const uint8_t* __restrict__ va,
+                       const float4* __restrict__ nb, const uint8_t* __restrict__ vb, int H, int W,
+                       long long pitch, double* __restrict__ partials) {
+  // Each thread sums its own pixels in FP32 (a few hundred terms at most for
+  // frames up to 2^24 pixels: relative error ~1e-5), then the block and the
+  // final pass add the per-thread sums in FP64.
+  float st = 0.0f, sp = 0.0f;
+  int cnt = 0;
+  for (int y = blockIdx.x; y < H; y += gridDim.x) {
+    for (int x = threadIdx.x; x < W; x += kThreads) {
+      const long long o = (long long)y * pitch + x;
+      if (__ldg(va + o) && __ldg(vb + o)) {
+        float pa, ta, pb, tb;
+        angles(__ldg(na + o), pa, ta);
+        angles(__ldg(nb + o), pb, tb);
+        const float dt = ta - tb, dp = pa - pb;
+        st = fmaf(dt, dt, st);
+        sp = fmaf(dp, dp, sp);
+        ++cnt;
+      }
+    }
+  }
+  double dst = st, dsp = sp, dcnt = cnt;
+  block_sum3(dst, dsp, dcnt);
+  if (threadIdx.x == 0) {
+    partials[3 * blockIdx.x + 0] = dst;
+    partials[3 * blockIdx.x + 1] = dsp;
+    partials[3 * blockIdx.x + 2] = dcnt;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) mse_final_kernel(const double* __restrict__ partials, int n,
+                                                             double* __restrict__ out) {
+  double st = 0.0, sp = 0.0, cnt = 0.0;
+  for (int i = threadIdx.x; i < n; i += kThreads) {
+    st += partials[3 * i + 0];
+    sp += partials[3 * i + 1];
+    cnt += partials[3 * i + 2];
+  }
+  block_sum3(st, sp, cnt);
+  if (threadIdx.x == 0) {
+    out[0] = cnt > 0.0 ? st / cnt : 0.0;
+    out[1] = cnt > 0.0 ? sp / cnt : 0.0;
+    out[2] = cnt;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_spherical(const float* normals, const uint8_t* valid, int H, int W, long long pitch, float* phi,
+                             float* theta, cudaStream_t stream) {
+  dim3 grid((W + kThreads - 1) / kThreads, H < 65535 ? H : 65535);
+  spherical_kernel<<<grid, kThreads, 0, stream>>>(reinterpret_cast<const float4*>(normals), valid, H, W, pitch,
+                                                   phi, theta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_angle_mse(const float* na, const uint8_t* va, const float* nb, const uint8_t* vb, int H, int W,
+                             long long pitch, double* partials, double* out, cudaStream_t stream) {
+  mse_partial_kernel<<<kMseBlocks, kThreads, 0, stream>>>(reinterpret_cast<const float4*>(na), va,
+                                                          reinterpret_cast<const float4*>(nb), vb, H, W, pitch,
+                                                          partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  mse_final_kernel<<<1, kThreads, 0, stream>>>(partials, kMseBlocks, out);
+  return cudaGetLastError();
+}
+
+}  // namespace nrm

@@ -167,4 +167,12 @@ cudaError_t launch_backward(const FrameDesc& fd, const BwdMaps& maps, const Glob
 cudaError_t launch_backward_batched(const BwdBatchArgs& args, int n_frames, int max_tiles, const Globals& g,
                                     cudaStream_t stream);
 
+// Evaluation kernels (nrm_eval.cu).
+constexpr int kMseBlocks = 1024;  // fixed, so that the reduction order never changes
+cudaError_t launch_spherical(const float* normals, const uint8_t* valid, int H, int W, long long pitch, float* phi,
+                             float* theta, cudaStream_t stream);
+// partials: 3 kMseBlocks doubles of device scratch; out: 3 doubles.
+cudaError_t launch_angle_mse(const float* na, const uint8_t* va, const float* nb, const uint8_t* vb, int H, int W,
+                             long long pitch, double* partials, double* out, cudaStream_t stream);
+
 }  // namespace nrm
