@@ -543,6 +543,22 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
     ms = e0.elapsed_time(e1) / reps
     out["angle_mse_4096x3072_mpx_s"] = round(4096 * 3072 / (ms / 1e3) / 1e6, 1)
     out["angle_mse_4096x3072_hbm_frac"] = round(4096 * 3072 * 34 / (ms / 1e3) / 1e9 / peak, 4)
+    # Plane-fitting ground truth (Sections 1 and 4) on the 4096 x 3072 frame:
+    # radius 2 is the paper's 25-point fit; 1 and 4 bracket it. Compute-bound
+    # (FP32 sums over the window and a Jacobi eigensolve per pixel).
+    pn = torch.empty_like(bn)
+    pv = torch.empty_like(bv)
+    for r in (1, 2, 4):
+        for _ in range(3):
+            be.plane_fit(big, r, pn, pv, stream)
+        e0.record(stream)
+        for _ in range(reps):
+            be.plane_fit(big, r, pn, pv, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        out[f"plane_fit_r{r}_4096x3072_mpx_s"] = round(4096 * 3072 / (ms / 1e3) / 1e6, 1)
+    del pn, pv
     be.sync_status()
     db.sync_status()
     de.sync_status()

@@ -190,6 +190,25 @@ NRM_API int nrm_spherical(const float* normals, const uint8_t* valid, int H, int
 NRM_API int nrm_angle_mse(nrm_handle* h, const float* normals, const uint8_t* valid, const float* ref_normals,
                           const uint8_t* ref_valid, int H, int W, long long pitch, double* out, void* cuda_stream);
 
+/* Plane-fitting ("plane-PCA") normals, the ground truth the paper evaluates
+ * against on real data (Section 1 describes the fit; Section 4 uses it with 25
+ * neighbouring points, i.e. radius 2). For each pixel: the back-projected
+ * points P = d (u, v, 1) of its (2 radius + 1) x (2 radius + 1) window, their
+ * scatter matrix about the centroid, and the unit eigenvector of its smallest
+ * eigenvalue, oriented like the method's normal (n . P > 0, or n . P < 0 with
+ * orient_to_camera). A pixel is valid iff every depth of its window lies in the
+ * image and is positive and finite (uint16: nonzero); other pixels get normal
+ * (0, 0, 0, 0) and mask byte 0.
+ * Uses the handle's H, W, intrinsics, in_dtype and orient_to_camera (the depth
+ * scale cancels from the direction). depth: H x W in_dtype values, pitch W;
+ * normals: H x W x 4 float32 (w = 0), 16-byte aligned; valid: H x W bytes.
+ * Device pointers, asynchronous on the stream. radius in 1..NRM_MAX_PLANE_RADIUS,
+ * else NRM_ERR_UNSUPPORTED. FP32 arithmetic on coordinates taken relative to the
+ * window's centre point; the eigenproblem by cyclic Jacobi rotations. */
+#define NRM_MAX_PLANE_RADIUS 4
+NRM_API int nrm_plane_fit(nrm_handle* h, const void* depth, float* normals, uint8_t* valid, int radius,
+                          void* cuda_stream);
+
 /* Waits for the handle's work, returns the device status word (NRM_OK or the
  * first device-side error since the last call) and clears it. */
 NRM_API int nrm_sync_status(nrm_handle* h);

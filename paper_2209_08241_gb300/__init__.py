@@ -206,6 +206,28 @@ class NormalEstimator(_Handle):
                                          _stream_ptr(stream)), "nrm_backward")
         return grad_depth
 
+    def plane_fit(self, depth: torch.Tensor, radius: int = 2, normals: torch.Tensor | None = None,
+                  valid: torch.Tensor | None = None, stream=None):
+        """Plane-fitting ground truth (Sections 1 and 4; radius 2 = 25 points):
+        (H, W, 4) float32 normals (w = 0) and (H, W) uint8 mask of the
+        (2 radius + 1)^2 window fit, oriented like the method's normals."""
+        _check_cuda(depth, "depth")
+        if tuple(depth.shape) != (self.H, self.W) or not depth.is_contiguous():
+            raise ValueError(f"depth must be a contiguous ({self.H}, {self.W}) tensor")
+        if _in_dtype(depth) != self.in_dtype:
+            raise TypeError("depth dtype does not match the estimator's in_dtype")
+        if normals is None:
+            normals = torch.empty((self.H, self.W, 4), dtype=torch.float32, device=self.device)
+        if valid is None:
+            valid = torch.empty((self.H, self.W), dtype=torch.uint8, device=self.device)
+        if normals.dtype != torch.float32 or tuple(normals.shape) != (self.H, self.W, 4) \
+                or not normals.is_contiguous() or tuple(valid.shape) != (self.H, self.W) \
+                or valid.dtype != torch.uint8 or not valid.is_contiguous():
+            raise ValueError("outputs must be contiguous (H, W, 4) float32 and (H, W) uint8")
+        _lib.check(self.lib.nrm_plane_fit(self.h, depth.data_ptr(), normals.data_ptr(), valid.data_ptr(),
+                                          int(radius), _stream_ptr(stream)), "nrm_plane_fit")
+        return normals, valid
+
 
 def _frame(depth: torch.Tensor, K, normals: torch.Tensor, valid: torch.Tensor) -> _lib.Frame:
     f = _lib.Frame()

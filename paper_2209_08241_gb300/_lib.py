@@ -24,6 +24,7 @@ NRM_OUT_F32X4, NRM_OUT_F16X4, NRM_OUT_OCT16 = 0, 1, 2
 NRM_MASK_RAW, NRM_MASK_SECANT = 0, 1
 NRM_MAX_ALPHA = 16
 NRM_NOALLOC_MAX_FRAMES = 256
+NRM_MAX_PLANE_RADIUS = 4
 
 
 class Intrinsics(ctypes.Structure):
@@ -79,6 +80,7 @@ SIGNATURES = [
                                      ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, _S]),
     ("nrm_angle_mse", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, _S]),
+    ("nrm_plane_fit", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _S]),
     ("nrm_sync_status", ctypes.c_int, [_H]),
     ("nrm_get_config", ctypes.c_int, [_H, ctypes.POINTER(TileConfig)]),
     ("nrm_set_config", ctypes.c_int, [_H, ctypes.POINTER(TileConfig)]),

@@ -870,6 +870,47 @@ int nrm_angle_mse(nrm_handle* h, const float* normals, const uint8_t* valid, con
   return NRM_OK;
 }
 
+int nrm_plane_fit(nrm_handle* h, const void* depth, float* normals, uint8_t* valid, int radius,
+                  void* cuda_stream) {
+  g_last_error.clear();
+  if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
+  if (h->H == 0 || h->W == 0) return fail(NRM_ERR_INVALID_ARG, "handle was created for batched calls only");
+  if (radius < 1 || radius > NRM_MAX_PLANE_RADIUS)
+    return fail(NRM_ERR_UNSUPPORTED, "radius %d outside 1..%d", radius, NRM_MAX_PLANE_RADIUS);
+  nrm_frame f;
+  f.depth = depth;
+  f.normals = normals;
+  f.valid = valid;
+  f.H = h->H;
+  f.W = h->W;
+  f.depth_pitch = h->W;
+  f.out_pitch = h->W;
+  f.K = h->K;
+  f.in_dtype = h->p.in_dtype;
+  int rc = validate_frame(f, 0, NRM_OUT_F32X4);
+  if (rc) return rc;
+  if ((h->H + 7) / 8 > 65535) return fail(NRM_ERR_UNSUPPORTED, "too many tile rows for the plane-fit launch");
+  DeviceGuard guard(h->device);
+  FrameDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.depth = depth;
+  d.normals = normals;
+  d.valid = valid;
+  d.H = f.H;
+  d.W = f.W;
+  d.depth_pitch = f.depth_pitch;
+  d.out_pitch = f.out_pitch;
+  d.inv_fx = (float)(1.0 / f.K.fx);
+  d.inv_fy = (float)(1.0 / f.K.fy);
+  d.cx = (float)f.K.cx;
+  d.cy = (float)f.K.cy;
+  d.in_dtype = f.in_dtype;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  NRM_CUDA(nrm::launch_plane_fit(d, radius, h->p.orient_to_camera ? -1.0f : 1.0f, st), "launch plane_fit_kernel");
+  NRM_CUDA(cudaEventRecord(h->last_single, st), "cudaEventRecord");
+  return NRM_OK;
+}
+
 int nrm_sync_status(nrm_handle* h) {
   if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
   DeviceGuard guard(h->device);

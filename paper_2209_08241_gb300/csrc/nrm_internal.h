@@ -175,4 +175,10 @@ cudaError_t launch_spherical(const float* normals, const uint8_t* valid, int H, 
 cudaError_t launch_angle_mse(const float* na, const uint8_t* va, const float* nb, const uint8_t* vb, int H, int W,
                              long long pitch, double* partials, double* out, cudaStream_t stream);
 
+// Plane-fitting ground truth (nrm_planefit.cu): FP32 normals (w = 0) and the
+// validity mask of the (2 radius + 1)^2 window fit; fd.depth, fd.normals,
+// fd.valid, pitches, H, W, cx, cy, inv_fx, inv_fy and in_dtype are used;
+// radius 1..4 (compiled per radius).
+cudaError_t launch_plane_fit(const FrameDesc& fd, int radius, float sign, cudaStream_t stream);
+
 }  // namespace nrm

@@ -90,3 +90,99 @@ def compare(normals, valid, ref, tau, half=False, what=""):
         tol = ANG_TOL_F16 if half else ANG_TOL_F32
         assert max_ang <= tol, f"{what}: max angular error {max_ang:.3g} rad > {tol}"
     return int(near.sum()), max_ang, int(both.sum())
+
+
+def plane_fit_banded(depth, K, radius, depth_scale=0.001, band=64):
+    """The plane-fitting oracle run on bands of rows (each with its radius-row
+    halo and cy shifted to the band's first row): identical to one call on the
+    whole image, in bounded memory."""
+    from oracle.plane_fit import plane_fit
+    D = np.asarray(depth)
+    H, W = D.shape
+    fx, fy, cx, cy = (float(v) for v in K)
+    n = np.zeros((H, W, 3))
+    v = np.zeros((H, W), np.uint8)
+    ev = np.zeros((H, W, 3))
+    for r0 in range(0, H, band):
+        r1 = min(H, r0 + band)
+        a, b = max(0, r0 - radius), min(H, r1 + radius)
+        nn, vv, ee = plane_fit(D[a:b], (fx, fy, cx, cy - a), radius, depth_scale)
+        n[r0:r1], v[r0:r1], ev[r0:r1] = nn[r0 - a:r1 - a], vv[r0 - a:r1 - a], ee[r0 - a:r1 - a]
+    return n, v, ev
+
+
+def window_moment(depth, K, radius, depth_scale=0.001):
+    """M = sum over each pixel's window of |P - P_centre|^2 (the scale of the
+    FP32 sums a kernel forms relative to the centre point); 0 where undefined."""
+    D = np.asarray(depth)
+    z = D.astype(np.float64) * (depth_scale if D.dtype == np.uint16 else 1.0)
+    H, W = z.shape
+    fx, fy, cx, cy = (float(v) for v in K)
+    X = z * ((np.arange(W) - cx) / fx)[None, :]
+    Y = z * ((np.arange(H) - cy) / fy)[:, None]
+    P = np.stack([X, Y, z], -1)
+    P = np.where(np.isfinite(P), P, 0.0)
+    R = radius
+    M = np.zeros((H, W))
+    Hi, Wi = H - 2 * R, W - 2 * R
+    if Hi <= 0 or Wi <= 0:
+        return M
+    c = P[R:R + Hi, R:R + Wi]
+    for dy in range(-R, R + 1):
+        for dx in range(-R, R + 1):
+            q = P[R + dy:R + dy + Hi, R + dx:R + dx + Wi] - c
+            M[R:R + Hi, R:R + Wi] += (q * q).sum(-1)
+    return M
+
+
+# Per-pixel bound for an FP32 plane fit against the FP64 oracle. The kernel's
+# window coordinates relative to the centre point carry relative errors of a
+# few ulp, so its scatter matrix is off by at most ~45 eps M (eps = 2^-24, M
+# the window moment above; products, 25-term sums and the mean subtraction),
+# and Jacobi adds a few eps ||S|| <= eps M. By the Davis-Kahan bound the
+# smallest eigenvector then moves by at most ~50 eps M / (lambda_2 - lambda_1)
+# = 3e-6 M / gap, which is the tolerance (on the synthetic scenes the largest
+# observed constant was 2.4e-7), plus 1e-6 rad for the final normalisation.
+PLANE_TOL_ABS = 1e-6
+PLANE_TOL_REL = 3e-6
+
+
+def compare_plane_fit(normals, valid, ref_n, ref_v, ref_ev, M, K, orient_sign=1.0, what=""):
+    """GPU (H, W, 4) float32 plane-fit normals and mask against the oracle.
+    Returns (pixels compared, pixels where the bound is below 1e-3 rad, max of
+    angle / bound)."""
+    if isinstance(normals, torch.Tensor):
+        normals = normals.cpu().numpy()
+    if isinstance(valid, torch.Tensor):
+        valid = valid.cpu().numpy()
+    assert (valid.astype(np.uint8) == ref_v).all(), \
+        f"{what}: {int((valid != ref_v).sum())} mask mismatches"
+    assert (normals[valid == 0] == 0).all(), f"{what}: invalid pixels must carry normal 0"
+    ok = valid == 1
+    if not ok.any():
+        return 0, 0, 0.0
+    g = normals[ok][:, :3].astype(np.float64)
+    assert (normals[ok][:, 3] == 0).all()
+    assert np.abs(np.linalg.norm(g, axis=-1) - 1).max() < 1e-5, f"{what}: normals not unit"
+    r = orient_sign * ref_n[ok]
+    ev = ref_ev[ok]
+    gap = ev[:, 1] - ev[:, 0]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tol = PLANE_TOL_ABS + PLANE_TOL_REL * M[ok] / gap
+    tol = np.where(gap > 0, tol, np.inf)
+    ang_signed = angles(g, r)
+    ang = np.minimum(ang_signed, np.pi - ang_signed)      # the eigenvector's line
+    bad = ang > tol
+    assert not bad.any(), f"{what}: {int(bad.sum())} normals outside the bound (worst angle " \
+                          f"{float(ang[bad].max()):.3g})"
+    # Orientation: where the line is determined and the view is not grazing
+    # (|n . ray| well above the bound), the side must match too.
+    H, W = valid.shape
+    fx, fy, cx, cy = (float(v) for v in K)
+    yy, xx = np.nonzero(ok)
+    ray = np.stack([(xx - cx) / fx, (yy - cy) / fy, np.ones_like(xx, dtype=np.float64)], -1)
+    ray /= np.linalg.norm(ray, axis=-1, keepdims=True)
+    decided = (tol < 1e-2) & (np.abs((r * ray).sum(-1)) > 2 * tol)
+    flipped = ang_signed > np.pi / 2
+    assert not (flipped & decided).any(), f"{what}: {int((flipped & decided).sum())} normals flipped"
+    return int(ok.sum()), int((tol < 1e-3).sum()), float(np.max(ang / tol))

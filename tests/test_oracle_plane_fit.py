@@ -102,3 +102,15 @@ def test_agrees_with_the_method_on_a_smooth_scene():
     ang = angle(pn[both], ref.n_hat[both])
     # Away from the depth steps the two estimates agree closely.
     assert np.median(ang) < 1e-3
+
+
+def test_banded_oracle_equals_one_call():
+    from parity import plane_fit_banded
+    d, K = scenes.random_frame(7, 40, 90, kind="f32", noise=True, holes=True)
+    D = d.numpy()
+    for R in (1, 3):
+        n1, v1, e1 = plane_fit(D, K, R)
+        n2, v2, e2 = plane_fit_banded(D, K, R, band=16)
+        np.testing.assert_array_equal(v1, v2)
+        np.testing.assert_allclose(n2, n1, atol=1e-12)
+        np.testing.assert_allclose(e2, e1, atol=1e-15, rtol=1e-9)
