@@ -360,6 +360,23 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
     px = N_FRAMES * H_FULLHD * W_FULLHD
     out["per_frame_plain_mpx_s"] = round(px / (ms / 1e3) / 1e6, 1)
     out["per_frame_plain_ms_per_step"] = round(ms, 4)
+    # Multi-scale variant (Section 2), per-frame launches on the same frames:
+    # four scales alpha = 1..4 with the single-pair (Eq. 1-3) and the
+    # four-direction (Eq. 4-6) stencils; 19 B/px like the headline.
+    for form in ("pair", "quad"):
+        for _ in range(3):
+            for i in range(N_FRAMES):
+                pf.estimate_multiscale(depth[i], (1, 2, 3, 4), form, normals[i], valid[i], stream)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(reps):
+            for i in range(N_FRAMES):
+                pf.estimate_multiscale(depth[i], (1, 2, 3, 4), form, normals[i], valid[i], stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        out[f"multiscale_{form}_1to4_mpx_s"] = round(px / (ms / 1e3) / 1e6, 1)
+        out[f"multiscale_{form}_1to4_hbm_frac"] = round(px * 19 / (ms / 1e3) / 1e9 / measured_peaks()[0], 4)
     pf.sync_status()
     del pf
 

@@ -190,6 +190,30 @@ NRM_API int nrm_spherical(const float* normals, const uint8_t* valid, int H, int
 NRM_API int nrm_angle_mse(nrm_handle* h, const float* normals, const uint8_t* valid, const float* ref_normals,
                           const uint8_t* ref_valid, int H, int W, long long pitch, double* out, void* cuda_stream);
 
+/* Multi-scale variant (Section 2: the authors' previous method averages its
+ * closed-form normal over pixel distances alpha_1..alpha_K to reduce noise).
+ * For each pixel the unnormalised per-scale normals are averaged,
+ *   n = (1/K) sum_i n(alpha_i),
+ * with every neighbour depth sampled at its own scale's distance alpha_i, and
+ * n(alpha) one of
+ *   NRM_MS_PAIR  the previous method's single tangent pair, Eq. 1-3:
+ *                neighbours (col + alpha, row) and (col, row + alpha);
+ *   NRM_MS_QUAD  the four-direction form of this paper, Eq. 4-6.
+ * The handle's mask mode and tau (Section 3.2, applied to the averaged n),
+ * depth dtype, depth scale, output dtype and orientation apply; its alpha is
+ * ignored. A pixel is valid only if every depth that any scale uses is inside
+ * the image and valid. Buffers as for nrm_estimate (device pointers, pitch W,
+ * asynchronous on the stream). */
+#define NRM_MAX_SCALES 8
+typedef enum { NRM_MS_PAIR = 0, NRM_MS_QUAD = 1 } nrm_ms_form;
+typedef struct {
+  int n_scales;                /* K, 1..NRM_MAX_SCALES */
+  int alpha[NRM_MAX_SCALES];   /* alpha_1..alpha_K, each 1..NRM_MAX_ALPHA; order does not matter */
+  int form;                    /* nrm_ms_form */
+} nrm_scales;
+NRM_API int nrm_estimate_multiscale(nrm_handle* h, const void* depth, void* normals, uint8_t* valid,
+                                    const nrm_scales* scales, void* cuda_stream);
+
 /* Plane-fitting ("plane-PCA") normals, the ground truth the paper evaluates
  * against on real data (Section 1 describes the fit; Section 4 uses it with 25
  * neighbouring points, i.e. radius 2). For each pixel: the back-projected

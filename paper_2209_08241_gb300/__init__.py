@@ -206,6 +206,35 @@ class NormalEstimator(_Handle):
                                          _stream_ptr(stream)), "nrm_backward")
         return grad_depth
 
+    def estimate_multiscale(self, depth: torch.Tensor, alphas=(1, 2, 3, 4), form: str = "pair",
+                            normals: torch.Tensor | None = None, valid: torch.Tensor | None = None, stream=None):
+        """Multi-scale variant (Section 2): the average of the per-scale
+        unnormalised normals over pixel distances ``alphas`` (at most 8),
+        each scale the previous method's single pair (``form="pair"``, Eq. 1-3)
+        or the four-direction form (``form="quad"``, Eq. 4-6); mask, dtypes and
+        orientation as for ``estimate``."""
+        _check_cuda(depth, "depth")
+        if tuple(depth.shape) != (self.H, self.W) or not depth.is_contiguous():
+            raise ValueError(f"depth must be a contiguous ({self.H}, {self.W}) tensor")
+        if _in_dtype(depth) != self.in_dtype:
+            raise TypeError("depth dtype does not match the estimator's in_dtype")
+        alphas = [int(a) for a in alphas]
+        if not 1 <= len(alphas) <= _lib.NRM_MAX_SCALES:
+            raise ValueError(f"between 1 and {_lib.NRM_MAX_SCALES} scales")
+        forms = {"pair": _lib.NRM_MS_PAIR, "quad": _lib.NRM_MS_QUAD}
+        if form not in forms:
+            raise ValueError(f"form must be one of {tuple(forms)}")
+        sc = _lib.Scales()
+        sc.n_scales = len(alphas)
+        for i, a in enumerate(alphas):
+            sc.alpha[i] = a
+        sc.form = forms[form]
+        if normals is None or valid is None:
+            normals, valid = self.new_outputs()
+        _lib.check(self.lib.nrm_estimate_multiscale(self.h, depth.data_ptr(), normals.data_ptr(), valid.data_ptr(),
+                                                    ctypes.byref(sc), _stream_ptr(stream)), "nrm_estimate_multiscale")
+        return normals, valid
+
     def plane_fit(self, depth: torch.Tensor, radius: int = 2, normals: torch.Tensor | None = None,
                   valid: torch.Tensor | None = None, stream=None):
         """Plane-fitting ground truth (Sections 1 and 4; radius 2 = 25 points):

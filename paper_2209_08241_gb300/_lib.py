@@ -58,6 +58,14 @@ class TileConfig(ctypes.Structure):
                 ("stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
 
 
+NRM_MAX_SCALES = 8
+NRM_MS_PAIR, NRM_MS_QUAD = 0, 1
+
+
+class Scales(ctypes.Structure):
+    _fields_ = [("n_scales", ctypes.c_int), ("alpha", ctypes.c_int * NRM_MAX_SCALES), ("form", ctypes.c_int)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("kernel_ms", ctypes.c_double),
                 ("tiles", ctypes.c_longlong)]
@@ -80,6 +88,8 @@ SIGNATURES = [
                                      ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, _S]),
     ("nrm_angle_mse", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, _S]),
+    ("nrm_estimate_multiscale", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.POINTER(Scales), _S]),
     ("nrm_plane_fit", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _S]),
     ("nrm_sync_status", ctypes.c_int, [_H]),
     ("nrm_get_config", ctypes.c_int, [_H, ctypes.POINTER(TileConfig)]),

@@ -870,6 +870,65 @@ int nrm_angle_mse(nrm_handle* h, const float* normals, const uint8_t* valid, con
   return NRM_OK;
 }
 
+int nrm_estimate_multiscale(nrm_handle* h, const void* depth, void* normals, uint8_t* valid,
+                            const nrm_scales* scales, void* cuda_stream) {
+  g_last_error.clear();
+  if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
+  if (h->H == 0 || h->W == 0) return fail(NRM_ERR_INVALID_ARG, "handle was created for batched calls only");
+  if (!scales) return fail(NRM_ERR_INVALID_ARG, "scales is NULL");
+  const int K = scales->n_scales;
+  if (K < 1 || K > NRM_MAX_SCALES) return fail(NRM_ERR_UNSUPPORTED, "n_scales %d outside 1..%d", K, NRM_MAX_SCALES);
+  if (scales->form != NRM_MS_PAIR && scales->form != NRM_MS_QUAD)
+    return fail(NRM_ERR_INVALID_ARG, "form %d", scales->form);
+  nrm::MsConsts ms;
+  std::memset(&ms, 0, sizeof(ms));
+  ms.K = K;
+  for (int i = 0; i < K; ++i) {
+    const int a = scales->alpha[i];
+    if (a < 1 || a > NRM_MAX_ALPHA) return fail(NRM_ERR_UNSUPPORTED, "alpha[%d] = %d outside 1..%d", i, a, NRM_MAX_ALPHA);
+    ms.alpha[i] = a;
+    ms.alpha_max = std::max(ms.alpha_max, a);
+  }
+  nrm_frame f;
+  f.depth = depth;
+  f.normals = normals;
+  f.valid = valid;
+  f.H = h->H;
+  f.W = h->W;
+  f.depth_pitch = h->W;
+  f.out_pitch = h->W;
+  f.K = h->K;
+  f.in_dtype = h->p.in_dtype;
+  int rc = validate_frame(f, 0, h->p.out_dtype);
+  if (rc) return rc;
+  if ((f.H + nrm::kMsTileY - 1) / nrm::kMsTileY > 65535)
+    return fail(NRM_ERR_UNSUPPORTED, "too many tile rows for the multi-scale launch");
+  // Per-scale constants in FP64, rounded once, with 1/K, the depth scale^2 and
+  // the orientation sign folded in (Eq. 1-3 or Eq. 4-6). The products are
+  // formed in the order of the single-scale constants, so one NRM_MS_QUAD
+  // scale reproduces nrm_estimate bit for bit.
+  const double s = f.in_dtype == NRM_IN_U16_MM ? (double)h->p.depth_scale : 1.0;
+  const double sign = h->p.orient_to_camera ? -1.0 : 1.0;
+  const double q = scales->form == NRM_MS_QUAD ? 4.0 : 1.0;
+  for (int i = 0; i < K; ++i) {
+    const double a = ms.alpha[i];
+    ms.A[i] = (float)(-sign * (a / (q * f.K.fy) * s * s) / K);
+    ms.B[i] = (float)(-sign * (a / (q * f.K.fx) * s * s) / K);
+    ms.C[i] = (float)(sign * (a * a / (q * f.K.fx * f.K.fy) * s * s) / K);
+  }
+  DeviceGuard guard(h->device);
+  const int TX = nrm::kMsTileX, TY = nrm::kMsTileY;
+  const int eb = f.in_dtype == NRM_IN_U16_MM ? 2 : 4;
+  FrameDesc d;
+  make_desc(&d, depth, normals, valid, f.H, f.W, f.depth_pitch, f.out_pitch, f.K, f.in_dtype, h->p, TX, TY,
+            TX + 2 * nrm::pad_x(ms.alpha_max, eb), TY + 2 * ms.alpha_max);
+  nrm::Globals g = make_globals(h);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  NRM_CUDA(nrm::launch_multiscale(d, ms, g, h->p.out_dtype, scales->form, st), "launch fwd_ms_kernel");
+  NRM_CUDA(cudaEventRecord(h->last_single, st), "cudaEventRecord");
+  return NRM_OK;
+}
+
 int nrm_plane_fit(nrm_handle* h, const void* depth, float* normals, uint8_t* valid, int radius,
                   void* cuda_stream) {
   g_last_error.clear();

@@ -365,8 +365,80 @@ __device__ __forceinline__ uint32_t bits_to_bytes4(uint32_t b) {
   return (b * 0x00204081u) & 0x01010101u;
 }
 
+// Stages the halo tile of a plain launch (one CTA per tile) and decodes it into
+// the float tile F (fw x bh, invalid depth -> NaN): one TMA box of bw x bh
+// elements at (gx0 - padx, gy0 - alpha) into smem (out-of-bounds zero fill =
+// invalid), or plain loads when the frame has no tensor map. Returns false on
+// every thread if the TMA wait expired, after thread 0 has recorded
+// NRM_ERR_TIMEOUT and waited (bounded) for the copy to land.
+template <int NT>
+__device__ __forceinline__ bool stage_plain_tile(unsigned char* smem, float* F, uint64_t* bar, const FrameDesc& fd,
+                                                 const TileFrame& tf, int alpha, int padx, int bw, int bh, int pad4,
+                                                 int fw, int gx0, int gy0, const Globals& g) {
+  const bool u16 = fd.in_dtype == NRM_IN_U16_MM;
+  const int eb = u16 ? 2 : 4;
+  bool ok = true;
+  if (fd.use_tma) {
+    const uint32_t b = smem_u32(bar);
+    if (threadIdx.x == 0) {
+      mbar_init(b, 1);
+      fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mbar_arrive_expect_tx(b, (uint32_t)(bw * bh * eb));
+      tma_load_2d(smem_u32(smem), &fd.tmap, gx0 - padx, gy0 - alpha, b);
+    }
+    ok = mbar_wait_warp(b, 0, g.timeout_ns);
+    if (ok) {
+      if (u16)
+        decode_tile<NT>(reinterpret_cast<const uint16_t*>(smem), F, fw, bh, bw, padx - pad4);
+      else
+        decode_tile<NT>(reinterpret_cast<const float*>(smem), F, fw, bh, bw, 0);
+    }
+  } else {
+    if (u16)
+      load_tile_decoded<uint16_t, NT>(F, fw, bh, tf, gx0 - pad4, gy0 - alpha);
+    else
+      load_tile_decoded<float, NT>(F, fw, bh, tf, gx0 - pad4, gy0 - alpha);
+  }
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      record_error(g.status, NRM_ERR_TIMEOUT);
+      mbar_wait_bounded(smem_u32(bar), 0, g.timeout_ns);  // let the copy land before exiting
+    }
+    return false;
+  }
+  return true;
+}
+
+// The Eq. 4-6 stencil of one pixel pair at distance alpha (Section 3.1): the
+// unnormalised n_x, n_y and P = n . (u1, v1, 1), all times the orientation
+// sign folded into A, B, C. pa, pb point at the pair's centre depths in the
+// decoded tile; dv = alpha rows.
+struct QuadStencil {
+  float2 A, B, C;
+  int alpha, dv;
+  __device__ __forceinline__ void operator()(const float* pa, const float* pb, float2 d1, float2& nx, float2& ny,
+                                             float2& P) const {
+    const float2 M1 = f2(-1.0f, -1.0f);
+    const float2 d2 = f2(pa[alpha], pb[alpha]);
+    const float2 d4 = f2(pa[-alpha], pb[-alpha]);
+    const float2 d3 = f2(pa[dv], pb[dv]);
+    const float2 d5 = f2(pa[-dv], pb[-dv]);
+    (void)d1;
+    // d2 - d4 as one fused (-1) d4 + d2: a single rounding, like a subtraction.
+    const float2 S24 = __fadd2_rn(d2, d4), D24 = __ffma2_rn(M1, d4, d2);
+    const float2 S35 = __fadd2_rn(d3, d5), D35 = __ffma2_rn(M1, d5, d3);
+    nx = __fmul2_rn(__fmul2_rn(A, S35), D24);
+    ny = __fmul2_rn(__fmul2_rn(B, S24), D35);
+    P = __fmul2_rn(__fmul2_rn(C, S24), S35);  // n . (u1, v1, 1), times the sign
+  }
+};
+
 // Computes one TX x TY output tile from the decoded float halo tile F
-// (origin global (gx0 - padx, gy0 - alpha), row pitch bw), threads 0..NT-1.
+// (origin global (gx0 - padx, gy0 - halo), row pitch bw), threads 0..NT-1,
+// with the stencil st giving each pixel pair's unnormalised normal.
 // Warp w handles rows w, w + NW, ...; lane l handles columns 32 k + l, so each
 // store instruction of a warp covers 32 consecutive pixels (512 B of float4).
 // Pixels 32 k + l and 32 (k+1) + l are evaluated as a pair with the paired
@@ -374,10 +446,10 @@ __device__ __forceinline__ uint32_t bits_to_bytes4(uint32_t b) {
 // of the scalar operations. Per-column terms are computed once per tile. Mask
 // bytes are gathered with one ballot per 32 pixels and written as TX/32
 // consecutive bytes per lane.
-template <int TX, int TY, int NT, int OUT, bool SECANT, bool FULL>
-__device__ __forceinline__ void compute_tile(const float* __restrict__ F, int bw, int padx,
-                                             const TileFrame& f, int gx0, int gy0, int alpha,
-                                             float tau2) {
+template <int TX, int TY, int NT, int OUT, bool SECANT, bool FULL, class Stencil>
+__device__ __forceinline__ void compute_tile_with(const float* __restrict__ F, int bw, int padx,
+                                                  const TileFrame& f, int gx0, int gy0, int halo, float tau2,
+                                                  const Stencil& st) {
   constexpr int NW = NT / 32;
   constexpr int CH = TX / 32;
   constexpr int NP = CH / 2;
@@ -399,9 +471,7 @@ __device__ __forceinline__ void compute_tile(const float* __restrict__ F, int bw
     colok[2 * p] = FULL || gxa < f.W;
     colok[2 * p + 1] = FULL || gxb < f.W;
   }
-  const float2 A = f2(f.a, f.a), B = f2(f.b, f.b), C = f2(f.c, f.c), T = f2(tau2, tau2);
-  const float2 M1 = f2(-1.0f, -1.0f);
-  const int dv = alpha * bw;
+  const float2 T = f2(tau2, tau2);
 
 #pragma unroll 1
   for (int ly = warp; ly < TY; ly += NW) {
@@ -410,7 +480,7 @@ __device__ __forceinline__ void compute_tile(const float* __restrict__ F, int bw
     const float v1 = ((float)gy - f.cy) * f.inv_fy;
     const float2 nv1 = f2(-v1, -v1);
     const float2 kv = f2(v1 * v1, v1 * v1);
-    const float* row = F + (ly + alpha) * bw + padx + lane;
+    const float* row = F + (ly + halo) * bw + padx + lane;
     const long long out_row = (long long)gy * f.out_pitch + gx0 + lane;
     uint32_t ballots[CH];
 #pragma unroll
@@ -418,17 +488,8 @@ __device__ __forceinline__ void compute_tile(const float* __restrict__ F, int bw
       const float* pa = row + 64 * p;
       const float* pb = pa + 32;
       const float2 d1 = f2(pa[0], pb[0]);
-      const float2 d2 = f2(pa[alpha], pb[alpha]);
-      const float2 d4 = f2(pa[-alpha], pb[-alpha]);
-      const float2 d3 = f2(pa[dv], pb[dv]);
-      const float2 d5 = f2(pa[-dv], pb[-dv]);
-      // Eq. 4-6 (Section 3.1).
-      // d2 - d4 as one fused (-1) d4 + d2: a single rounding, like a subtraction.
-      const float2 S24 = __fadd2_rn(d2, d4), D24 = __ffma2_rn(M1, d4, d2);
-      const float2 S35 = __fadd2_rn(d3, d5), D35 = __ffma2_rn(M1, d5, d3);
-      const float2 nx = __fmul2_rn(__fmul2_rn(A, S35), D24);
-      const float2 ny = __fmul2_rn(__fmul2_rn(B, S24), D35);
-      const float2 P = __fmul2_rn(__fmul2_rn(C, S24), S35);  // n . (u1, v1, 1), times the sign
+      float2 nx, ny, P;
+      st(pa, pb, d1, nx, ny, P);
       const float2 nz = __ffma2_rn(nu1[p], nx, __ffma2_rn(nv1, ny, P));
       const float2 q = __ffma2_rn(nx, nx, __ffma2_rn(ny, ny, __fmul2_rn(nz, nz)));
       // Section 3.2 mask in squared form; NaN (invalid depth) fails every test.
@@ -499,6 +560,15 @@ __device__ __forceinline__ void compute_tile(const float* __restrict__ F, int bw
       }
     }
   }
+}
+
+
+template <int TX, int TY, int NT, int OUT, bool SECANT, bool FULL>
+__device__ __forceinline__ void compute_tile(const float* __restrict__ F, int bw, int padx,
+                                             const TileFrame& f, int gx0, int gy0, int alpha,
+                                             float tau2) {
+  const QuadStencil st{f2(f.a, f.a), f2(f.b, f.b), f2(f.c, f.c), alpha, alpha * bw};
+  compute_tile_with<TX, TY, NT, OUT, SECANT, FULL>(F, bw, padx, f, gx0, gy0, alpha, tau2, st);
 }
 
 // compute_tile for the tile's mask mode, with the column checks compiled out

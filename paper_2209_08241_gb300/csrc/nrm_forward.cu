@@ -47,38 +47,7 @@ __global__ void __launch_bounds__(NT)
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SB + ftile_bytes_for(TX, TY, alpha));
   const TileFrame tf = tile_frame(fd, g.sign);
 
-  bool ok = true;
-  if (fd.use_tma) {
-    const uint32_t b = smem_u32(bar);
-    if (threadIdx.x == 0) {
-      mbar_init(b, 1);
-      fence_barrier_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      mbar_arrive_expect_tx(b, (uint32_t)(bw * bh * eb));
-      tma_load_2d(smem_u32(smem), &fd.tmap, gx0 - padx, gy0 - alpha, b);
-    }
-    ok = mbar_wait_warp(b, 0, g.timeout_ns);
-    if (ok) {
-      if (u16)
-        decode_tile<NT>(reinterpret_cast<const uint16_t*>(smem), F, fw, bh, bw, padx - pad4);
-      else
-        decode_tile<NT>(reinterpret_cast<const float*>(smem), F, fw, bh, bw, 0);
-    }
-  } else {
-    if (u16)
-      load_tile_decoded<uint16_t, NT>(F, fw, bh, tf, gx0 - pad4, gy0 - alpha);
-    else
-      load_tile_decoded<float, NT>(F, fw, bh, tf, gx0 - pad4, gy0 - alpha);
-  }
-  if (__syncthreads_or(!ok)) {
-    if (threadIdx.x == 0) {
-      record_error(g.status, NRM_ERR_TIMEOUT);
-      mbar_wait_bounded(smem_u32(bar), 0, g.timeout_ns);  // let the copy land before exiting
-    }
-    return;
-  }
+  if (!stage_plain_tile<NT>(smem, F, bar, fd, tf, alpha, padx, bw, bh, pad4, fw, gx0, gy0, g)) return;
   compute_tile_any<TX, TY, NT, OUT>(F, fw, pad4, tf, gx0, gy0, g);
 }
 

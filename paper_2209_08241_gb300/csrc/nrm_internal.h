@@ -175,6 +175,25 @@ cudaError_t launch_spherical(const float* normals, const uint8_t* valid, int H, 
 cudaError_t launch_angle_mse(const float* na, const uint8_t* va, const float* nb, const uint8_t* vb, int H, int W,
                              long long pitch, double* partials, double* out, cudaStream_t stream);
 
+// Multi-scale variant (nrm_multiscale.cu): one CTA per kMsTileX x kMsTileY
+// tile, halo of the largest scale. Per scale i the constants of its stencil
+// (NRM_MS_PAIR: Eq. 1-3; NRM_MS_QUAD: Eq. 4-6), with 1/K, the depth scale^2 and
+// the orientation sign folded in: n_x += A_i (...), n_y += B_i (...),
+// n . ray += C_i (...).
+constexpr int kMsTileX = 128;
+constexpr int kMsTileY = 16;
+constexpr int kMsThreads = 256;
+struct MsConsts {
+  int K;
+  int alpha_max;
+  int alpha[NRM_MAX_SCALES];
+  float A[NRM_MAX_SCALES], B[NRM_MAX_SCALES], C[NRM_MAX_SCALES];
+};
+// fd.tmap must map the depth with box (kMsTileX + 2 pad_x(alpha_max, eb)) x
+// (kMsTileY + 2 alpha_max) (or fd.use_tma = 0).
+cudaError_t launch_multiscale(const FrameDesc& fd, const MsConsts& ms, const Globals& g, int out_dtype, int form,
+                              cudaStream_t stream);
+
 // Plane-fitting ground truth (nrm_planefit.cu): FP32 normals (w = 0) and the
 // validity mask of the (2 radius + 1)^2 window fit; fd.depth, fd.normals,
 // fd.valid, pitches, H, W, cx, cy, inv_fx, inv_fy and in_dtype are used;

@@ -8,6 +8,8 @@ Cases:
   adjoint_batch  batched adjoint on N 640 x 480 float32 frames (default 32)
   plane_fit      plane-fitting ground truth, radius --radius (default 2), on a
                  4096 x 3072 float32 frame
+  multiscale     multi-scale variant, scales 1..4, stencil --form (pair or
+                 quad), on a 4096 x 3072 float32 frame
 
 Each case runs the kernel ``--reps`` times after one untimed call and prints the
 mean time per call (CUDA events) and the algorithmic bandwidth.
@@ -86,10 +88,20 @@ def case_plane_fit(radius: int, reps: int):
     return ms, px, px * 21
 
 
+def case_multiscale(form: str, reps: int):
+    d, K = scenes.random_frame(4999, 4096, 3072, "cuda", kind="f32", holes=False, clip_range=False)
+    est = nrm.NormalEstimator(K, 3072, 4096)
+    n, m = est.estimate_multiscale(d, (1, 2, 3, 4), form)
+    ms = _time(lambda: est.estimate_multiscale(d, (1, 2, 3, 4), form, n, m), reps)
+    px = 4096 * 3072
+    return ms, px, px * 21
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["forward", "adjoint", "adjoint_batch", "plane_fit"])
+    ap.add_argument("case", choices=["forward", "adjoint", "adjoint_batch", "plane_fit", "multiscale"])
     ap.add_argument("--radius", type=int, default=2)
+    ap.add_argument("--form", choices=["pair", "quad"], default="pair")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--frames", type=int, default=0)
     a = ap.parse_args(argv)
@@ -99,6 +111,8 @@ def main(argv=None):
         ms, px, nbytes = case_adjoint(a.reps)
     elif a.case == "plane_fit":
         ms, px, nbytes = case_plane_fit(a.radius, a.reps)
+    elif a.case == "multiscale":
+        ms, px, nbytes = case_multiscale(a.form, a.reps)
     else:
         ms, px, nbytes = case_adjoint_batch(a.frames or 32, a.reps)
     print(f"{a.case}: {ms:.4f} ms/call, {px / ms / 1e3:.1f} Mpx/s, {nbytes / ms / 1e6:.1f} GB/s algorithmic")

@@ -186,3 +186,55 @@ def compare_plane_fit(normals, valid, ref_n, ref_v, ref_ev, M, K, orient_sign=1.
     flipped = ang_signed > np.pi / 2
     assert not (flipped & decided).any(), f"{what}: {int((flipped & decided).sum())} normals flipped"
     return int(ok.sum()), int((tol < 1e-3).sum()), float(np.max(ang / tol))
+
+
+def ms_kappa(depth, K, alphas, form, depth_scale=0.001):
+    """Cancellation factor of a multi-scale average, from the oracle: sum of the
+    per-scale |n_i| over |sum of n_i| (1 where the scales agree, large where
+    they cancel; inf where the sum vanishes)."""
+    from oracle import STAT_RAW
+    from oracle.multiscale import multiscale
+    D = np.asarray(depth)
+    tot = None
+    mag = None
+    for a in alphas:
+        r = multiscale(D, K, [a], form, STAT_RAW, np.inf, depth_scale)
+        tot = r.n_raw if tot is None else tot + r.n_raw
+        m = np.linalg.norm(r.n_raw, axis=-1)
+        mag = m if mag is None else mag + m
+    den = np.linalg.norm(tot, axis=-1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(den > 0, mag / den, np.inf)
+
+
+def compare_ms(normals, valid, ref, tau, kappa, half=False, what=""):
+    """Multi-scale output against the multi-scale oracle. As ``compare``, but a
+    pixel is excluded from the mask comparison when its statistic is within
+    1e-6 kappa relative of tau: the FP32 sums over scales carry relative errors
+    of a few ulp of the per-scale magnitudes, i.e. kappa times more relative to
+    the average. Returns (near_tau_count, max_angle, n_valid, max kappa over
+    the compared pixels)."""
+    if isinstance(normals, torch.Tensor):
+        normals = normals.detach().float().cpu().numpy()
+    if isinstance(valid, torch.Tensor):
+        valid = valid.cpu().numpy()
+    n = normals[..., :3].astype(np.float64)
+    m = valid.astype(np.uint8)
+    assert set(np.unique(m)).issubset({0, 1}), f"{what}: mask bytes must be 0/1"
+    band = NEAR_TAU_REL * np.maximum(1.0, np.nan_to_num(kappa, nan=1.0, posinf=1e30))
+    with np.errstate(invalid="ignore"):
+        near = np.isfinite(ref.stat) & (np.abs(ref.stat - tau) <= band * tau)
+    mism = (m != ref.valid) & ~near
+    assert mism.sum() == 0, (f"{what}: {int(mism.sum())} mask mismatches, e.g. at "
+                             f"{np.argwhere(mism)[:5].tolist()}")
+    assert (normals[m == 0] == 0).all(), f"{what}: masked pixels must carry (0,0,0,0)"
+    assert (normals[..., 3] == 0).all(), f"{what}: 4th component must be 0"
+    both = (m == 1) & (ref.valid == 1)
+    max_ang, max_k = 0.0, 1.0
+    if both.any():
+        ang = angles(n[both], ref.n_hat[both])
+        max_ang = float(ang.max())
+        max_k = float(np.max(kappa[both]))
+        tol = ANG_TOL_F16 if half else ANG_TOL_F32
+        assert max_ang <= tol, f"{what}: max angular error {max_ang:.3g} rad > {tol} (max kappa {max_k:.3g})"
+    return int(near.sum()), max_ang, int(both.sum()), max_k

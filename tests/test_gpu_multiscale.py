@@ -1,0 +1,138 @@
+"""GPU multi-scale variant (Section 2's average over pixel distances, with the
+previous method's single-pair stencil of Eq. 1-3 or the four-direction stencil
+of Eq. 4-6) against the FP64 multi-scale oracle, element by element.
+
+Tolerances: normals 1e-4 rad (FP32 output) / 5e-3 rad (half), masks bit-exact
+except pixels whose oracle statistic lies within 1e-6 kappa relative of tau,
+kappa being the per-pixel cancellation factor of the scale average (see
+parity.compare_ms). With one scale the four-direction variant must equal the
+single-scale kernel bit for bit."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2209_08241_gb300 as nrm
+from oracle.multiscale import multiscale
+from parity import ANG_TOL_OCT16, angles, compare_ms, decode_oct16, ms_kappa
+from synth import scenes
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def stat_mode(p):
+    return oracle.STAT_SECANT if p.mask_mode == "secant" else oracle.STAT_RAW
+
+
+def run(depth, K, p, alphas, form):
+    in_dtype = "u16" if depth.dtype == torch.uint16 else "f32"
+    H, W = depth.shape
+    est = nrm.NormalEstimator(K, H, W, p, in_dtype=in_dtype)
+    n, m = est.estimate_multiscale(depth, alphas, form)
+    est.sync_status()
+    D = depth.cpu().numpy()
+    ref = multiscale(D, K, alphas, form, stat_mode(p), p.tau, p.depth_scale, int(p.orient_to_camera))
+    kappa = ms_kappa(D, K, alphas, form, p.depth_scale)
+    return n, m, ref, kappa
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return scenes.cfg1_depth(DEV)
+
+
+@pytest.mark.parametrize("form", ["pair", "quad"])
+@pytest.mark.parametrize("alphas", [(1, 2, 3, 4), (2,), (1, 3, 8)])
+@pytest.mark.parametrize("mode", ["secant", "raw"])
+def test_cfg1_parity(cfg1, form, alphas, mode):
+    d, K = cfg1
+    tau = 12.0
+    if mode == "raw":
+        # Split the valid pixels: tau at the median length of the averaged n.
+        r = multiscale(d.cpu().numpy(), K, alphas, form, oracle.STAT_RAW, np.inf).r
+        tau = float(np.nanmedian(r))
+    p = nrm.NormalParams(mask_mode=mode, tau=tau)
+    n, m, ref, kappa = run(d, K, p, list(alphas), form)
+    near, ang, nv, mk = compare_ms(n, m, ref, tau, kappa, what=f"cfg1 {form} {alphas} {mode}")
+    assert nv > 0.3 * d.numel()
+    print(f"{form} {alphas} {mode}: max angle {ang:.2e} rad, near-tau {near}, max kappa {mk:.3g}")
+
+
+@pytest.mark.parametrize("form", ["pair", "quad"])
+def test_cfg1_half_output(cfg1, form):
+    d, K = cfg1
+    p = nrm.NormalParams(out_dtype="f16")
+    n, m, ref, kappa = run(d, K, p, [1, 2, 3, 4], form)
+    compare_ms(n, m, ref, p.tau, kappa, half=True, what=f"cfg1 {form} f16")
+
+
+@pytest.mark.parametrize("shape", [(197, 333), (481, 641), (37, 70)])
+@pytest.mark.parametrize("form,alphas", [("pair", (1, 2, 3, 4)), ("quad", (1, 2)), ("pair", (16,)), ("quad", (1, 16))])
+@pytest.mark.parametrize("orient", [False, True])
+def test_u16_ragged_with_holes(shape, form, alphas, orient):
+    H, W = shape
+    d, K = scenes.random_frame(700 + H + W, W, H, DEV, kind="u16")
+    p = nrm.NormalParams(orient_to_camera=orient)
+    n, m, ref, kappa = run(d, K, p, list(alphas), form)
+    compare_ms(n, m, ref, p.tau, kappa, what=f"u16 {shape} {form} {alphas} orient={orient}")
+
+
+@pytest.mark.parametrize("alpha", [1, 2, 5])
+@pytest.mark.parametrize("kind", ["f32", "u16"])
+@pytest.mark.parametrize("out", ["f32", "oct16"])
+def test_one_quad_scale_equals_the_single_scale_kernel(alpha, kind, out):
+    """K = 1 with the four-direction stencil is the method itself: same
+    constants, same operations, so the outputs are identical bit for bit."""
+    d, K = scenes.random_frame(900 + alpha, 641, 479, DEV, kind=kind)
+    p = nrm.NormalParams(alpha=alpha, out_dtype=out)
+    est = nrm.NormalEstimator(K, 479, 641, p, in_dtype=kind)
+    n1, m1 = est.estimate(d)
+    n2, m2 = est.estimate_multiscale(d, [alpha], "quad")
+    est.sync_status()
+    assert torch.equal(m1, m2)
+    assert torch.equal(n1, n2)
+
+
+def test_oct16_output_matches_float_output():
+    d, K = scenes.random_frame(77, 640, 480, DEV, kind="u16")
+    ef = nrm.NormalEstimator(K, 480, 640, nrm.NormalParams(), in_dtype="u16")
+    eo = nrm.NormalEstimator(K, 480, 640, nrm.NormalParams(out_dtype="oct16"), in_dtype="u16")
+    nf, mf = ef.estimate_multiscale(d, [1, 2, 3, 4], "pair")
+    no, mo = eo.estimate_multiscale(d, [1, 2, 3, 4], "pair")
+    ef.sync_status()
+    eo.sync_status()
+    assert torch.equal(mf, mo)
+    v = mf.cpu().numpy() == 1
+    codes = no.cpu().numpy()
+    assert (codes[~v] == 0).all()
+    ang = angles(decode_oct16(codes[v]), nf.cpu().numpy()[v][:, :3])
+    assert ang.max() <= ANG_TOL_OCT16
+
+
+def test_fullsize_1080p_u16():
+    """The bench's frame size and input type, compared pixel by pixel."""
+    d, K = scenes.random_frame(1000, 1920, 1080, DEV, kind="u16")
+    p = nrm.NormalParams()
+    n, m, ref, kappa = run(d, K, p, [1, 2, 3, 4], "pair")
+    near, ang, nv, mk = compare_ms(n, m, ref, p.tau, kappa, what="1080p u16 pair 1-4")
+    assert nv > 0.5 * 1920 * 1080
+
+
+def test_bad_scales_are_rejected():
+    est = nrm.NormalEstimator((100.0, 100.0, 10.0, 10.0), 20, 20)
+    d = torch.ones((20, 20), device=DEV)
+    for alphas in ([], [1] * 9, [0], [17], [1, -2]):
+        with pytest.raises((nrm._lib.NrmError, ValueError)):
+            est.estimate_multiscale(d, alphas)
+    n, m = est.new_outputs()
+    sc = nrm._lib.Scales()
+    sc.n_scales = 1
+    sc.alpha[0] = 1
+    sc.form = 2
+    rc = est.lib.nrm_estimate_multiscale(est.h, d.data_ptr(), n.data_ptr(), m.data_ptr(), ctypes.byref(sc), None)
+    assert rc == nrm._lib.NRM_ERR_INVALID_ARG
+    assert est.lib.nrm_estimate_multiscale(est.h, d.data_ptr(), n.data_ptr(), m.data_ptr(), None, None) \
+        == nrm._lib.NRM_ERR_INVALID_ARG
