@@ -41,7 +41,8 @@ METRIC = "normals Mpixel/s and % HBM roofline (batched vs per-frame, 1 GB300); p
 UNIT = "Mpixel/s"
 N_FRAMES, W_FULLHD, H_FULLHD = 64, 1920, 1080
 BYTES_PER_PX = 2 + 16 + 1       # uint16 depth in, float4 normal + uint8 mask out
-KERNEL_SOURCES = ("paper_2209_08241_gb300/csrc/nrm_forward.cu", "paper_2209_08241_gb300/csrc/nrm_device.cuh")
+KERNEL_SOURCES = ("paper_2209_08241_gb300/csrc/nrm_forward.cu", "paper_2209_08241_gb300/csrc/nrm_forward_kernels.cuh",
+                  "paper_2209_08241_gb300/csrc/nrm_device.cuh")
 
 # DRAM bytes per launch of the batched kernel from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only while the kernel sources hash to the key.
@@ -433,6 +434,34 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
     out["u16_oct16_hbm_frac"] = round(px * 7 / (kms / 1e3) / 1e9 / peak, 4)
     ho.sync_status()
     del ho, no
+
+    # Normals, mask and the organised point cloud in one pass on the same
+    # batch (2 + 16 + 1 + 16 = 35 B/px).
+    hp = nrm.BatchedEstimator(nrm.NormalParams(), device=dev)
+    pts = torch.empty((N_FRAMES, H_FULLHD, W_FULLHD, 4), dtype=torch.float32, device=dev)
+    pitems = [(depth[i], Ks[i]) for i in range(N_FRAMES)]
+    pouts = [(normals[i], valid[i], pts[i]) for i in range(N_FRAMES)]
+    frp, _ = hp.make_frames(pitems, pouts)
+    if not args.no_autotune:
+        hp.autotune(pitems, pouts)
+    out["u16_points_tile"] = hp.config()
+    hp.enable_timing(True)
+    for _ in range(5):
+        hp.run(frp, N_FRAMES, stream)
+    torch.cuda.synchronize(dev)
+    hp.reset_stats()
+    e0.record(stream)
+    for _ in range(reps):
+        hp.run(frp, N_FRAMES, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    st = hp.stats()
+    kms = st["kernel_ms"] / max(1, st["launches"])
+    out["u16_points_f32x4_mpx_s"] = round(px / (ms / 1e3) / 1e6, 1)
+    out["u16_points_f32x4_hbm_frac"] = round(px * 35 / (kms / 1e3) / 1e9 / peak, 4)
+    hp.sync_status()
+    del hp, pts
 
     # Uneven-size batch: 256 float32 frames from the size mix, one launch.
     mix = scenes.mixed_batch(256, device=dev, kind="f32")

@@ -104,8 +104,13 @@ NRM_API void nrm_default_params(nrm_params* p);
 typedef struct nrm_handle nrm_handle;
 
 /* One frame of a batch. Pitches are in elements of the respective buffer:
- * depth_pitch in depth elements (>= W); out_pitch in pixels for both the normal
- * map and the mask (>= W). */
+ * depth_pitch in depth elements (>= W); out_pitch in pixels for the normal
+ * map, the mask and the point cloud (>= W).
+ * points (optional, may be NULL): the organised point cloud of the frame,
+ * written in the same pass, H x W x 4 float32 (x, y, z, 0) in metres,
+ * P = d (u, v, 1) (Section 2, the back-projection below Eq. 3), the origin
+ * where the depth is invalid (independent of the normal mask); 16-byte
+ * aligned device memory. */
 typedef struct {
   const void* depth;
   void* normals;
@@ -115,6 +120,7 @@ typedef struct {
   long long out_pitch;
   nrm_intrinsics K;
   int in_dtype;
+  float* points;
 } nrm_frame;
 
 /* Creates a handle for H x W frames with intrinsics K (used by nrm_estimate and
@@ -131,6 +137,12 @@ NRM_API void nrm_destroy(nrm_handle* h);
  * (dense) of the handle's out_dtype; valid: H x W bytes (dense). */
 NRM_API int nrm_estimate(nrm_handle* h, const void* depth, void* normals, uint8_t* valid,
                  void* cuda_stream);
+
+/* nrm_estimate that also writes the frame's organised point cloud (see
+ * nrm_frame.points: H x W x 4 float32, pitch W, 16-byte aligned device memory;
+ * NULL is NRM_ERR_INVALID_ARG). */
+NRM_API int nrm_estimate_points(nrm_handle* h, const void* depth, void* normals, uint8_t* valid, float* points,
+                                void* cuda_stream);
 
 /* n frames of any sizes, intrinsics and input dtypes in ONE persistent launch
  * over a (frame, tile) work list, replayed from a CUDA graph that the handle
@@ -308,8 +320,9 @@ NRM_API int nrm_reset_stats(nrm_handle* h);
  * kernel's shared-memory limit. Make that first call before any stream capture
  * begins.
  *
- * Errors: NRM_ERR_UNSUPPORTED for n > NRM_NOALLOC_MAX_FRAMES (nothing is
- * launched); otherwise as nrm_estimate_batched. */
+ * Errors: NRM_ERR_UNSUPPORTED for n > NRM_NOALLOC_MAX_FRAMES or a frame with
+ * a point-cloud buffer (this entry point writes normals and masks only;
+ * nothing is launched); otherwise as nrm_estimate_batched. */
 NRM_API int nrm_estimate_batched_noalloc(const nrm_frame* frames, int n, const nrm_params* p,
                                          int* device_status, void* cuda_stream);
 

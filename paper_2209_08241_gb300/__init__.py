@@ -175,8 +175,10 @@ class NormalEstimator(_Handle):
         return n, m
 
     def estimate(self, depth: torch.Tensor, normals: torch.Tensor | None = None,
-                 valid: torch.Tensor | None = None, stream=None):
-        """Writes the (H, W, 4) normal map and (H, W) uint8 mask; returns both."""
+                 valid: torch.Tensor | None = None, stream=None, points: torch.Tensor | None = None):
+        """Writes the (H, W, 4) normal map and (H, W) uint8 mask; returns both.
+        With ``points`` ((H, W, 4) float32) the organised point cloud is written
+        in the same pass."""
         _check_cuda(depth, "depth")
         if tuple(depth.shape) != (self.H, self.W) or not depth.is_contiguous():
             raise ValueError(f"depth must be a contiguous ({self.H}, {self.W}) tensor")
@@ -184,6 +186,11 @@ class NormalEstimator(_Handle):
             raise TypeError("depth dtype does not match the estimator's in_dtype")
         if normals is None or valid is None:
             normals, valid = self.new_outputs()
+        if points is not None:
+            _check_points(points, self.H, self.W, self.W)
+            _lib.check(self.lib.nrm_estimate_points(self.h, depth.data_ptr(), normals.data_ptr(), valid.data_ptr(),
+                                                    points.data_ptr(), _stream_ptr(stream)), "nrm_estimate_points")
+            return normals, valid
         _lib.check(self.lib.nrm_estimate(self.h, depth.data_ptr(), normals.data_ptr(),
                                          valid.data_ptr(), _stream_ptr(stream)), "nrm_estimate")
         return normals, valid
@@ -258,7 +265,15 @@ class NormalEstimator(_Handle):
         return normals, valid
 
 
-def _frame(depth: torch.Tensor, K, normals: torch.Tensor, valid: torch.Tensor) -> _lib.Frame:
+def _check_points(points: torch.Tensor, H: int, W: int, out_pitch: int):
+    _check_cuda(points, "points")
+    if points.dtype != torch.float32 or tuple(points.shape) != (H, W, 4) or points.stride(2) != 1 \
+            or points.stride(1) != 4 or (H * W and points.stride(0) != 4 * out_pitch):
+        raise ValueError("points must be (H, W, 4) float32 with the normals' pixel pitch")
+
+
+def _frame(depth: torch.Tensor, K, normals: torch.Tensor, valid: torch.Tensor,
+           points: torch.Tensor | None = None) -> _lib.Frame:
     f = _lib.Frame()
     f.depth = depth.data_ptr()
     f.normals = normals.data_ptr()
@@ -271,6 +286,9 @@ def _frame(depth: torch.Tensor, K, normals: torch.Tensor, valid: torch.Tensor) -
         f.depth_pitch = f.out_pitch = f.W
     f.K = _intr(K)
     f.in_dtype = _in_dtype(depth)
+    if points is not None:
+        _check_points(points, f.H, f.W, f.out_pitch)
+        f.points = points.data_ptr()
     return f
 
 
@@ -283,9 +301,10 @@ class BatchedEstimator(_Handle):
         super().__init__(None, 0, 0, params, NRM_IN_F32_M, device)
         self._frames = None
 
-    def make_frames(self, items: Sequence, outputs: Sequence | None = None):
+    def make_frames(self, items: Sequence, outputs: Sequence | None = None, points: bool = False):
         """ctypes frame array for [(depth, K), ...] with outputs [(normals, valid), ...]
-        (allocated when None). Returns (frames_array, outputs)."""
+        or [(normals, valid, points), ...] (allocated when None; ``points`` asks for
+        the organised point cloud, (H, W, 4) float32). Returns (frames_array, outputs)."""
         n = len(items)
         arr = (_lib.Frame * max(n, 1))()
         outs = []
@@ -295,9 +314,14 @@ class BatchedEstimator(_Handle):
                 raise ValueError("each depth must be a 2-D tensor with unit column stride")
             H, W = depth.shape
             C = self.params.out_channels
+            pm = None
             if outputs is None:
                 nm = torch.empty((H, W, C), dtype=self.params.torch_out_dtype, device=depth.device)
                 vm = torch.empty((H, W), dtype=torch.uint8, device=depth.device)
+                if points:
+                    pm = torch.empty((H, W, 4), dtype=torch.float32, device=depth.device)
+            elif len(outputs[i]) == 3:
+                nm, vm, pm = outputs[i]
             else:
                 nm, vm = outputs[i]
             if tuple(nm.shape) != (H, W, C) or tuple(vm.shape) != (H, W):
@@ -307,16 +331,16 @@ class BatchedEstimator(_Handle):
                 raise ValueError(f"normals (H, W, {C}) and valid (H, W) must share the pixel pitch")
             if nm.dtype != self.params.torch_out_dtype or vm.dtype != torch.uint8:
                 raise TypeError("output dtypes do not match the estimator's out_dtype / uint8")
-            arr[i] = _frame(depth, K, nm, vm)
-            outs.append((nm, vm))
+            arr[i] = _frame(depth, K, nm, vm, pm)
+            outs.append((nm, vm) if pm is None else (nm, vm, pm))
         return arr, outs
 
     def run(self, frames_array, n: int, stream=None):
         _lib.check(self.lib.nrm_estimate_batched(self.h, frames_array, int(n), _stream_ptr(stream)),
                    "nrm_estimate_batched")
 
-    def __call__(self, items: Sequence, outputs: Sequence | None = None, stream=None):
-        arr, outs = self.make_frames(items, outputs)
+    def __call__(self, items: Sequence, outputs: Sequence | None = None, stream=None, points: bool = False):
+        arr, outs = self.make_frames(items, outputs, points)
         self.run(arr, len(items), stream)
         return outs
 

@@ -42,7 +42,7 @@ class Frame(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_void_p), ("normals", ctypes.c_void_p),
                 ("valid", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
                 ("depth_pitch", ctypes.c_longlong), ("out_pitch", ctypes.c_longlong),
-                ("K", Intrinsics), ("in_dtype", ctypes.c_int)]
+                ("K", Intrinsics), ("in_dtype", ctypes.c_int), ("points", ctypes.c_void_p)]
 
 
 class GradFrame(ctypes.Structure):
@@ -80,6 +80,8 @@ SIGNATURES = [
                                   ctypes.POINTER(Params), ctypes.POINTER(_H)]),
     ("nrm_destroy", None, [_H]),
     ("nrm_estimate", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _S]),
+    ("nrm_estimate_points", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, _S]),
     ("nrm_estimate_batched", ctypes.c_int, [_H, ctypes.POINTER(Frame), ctypes.c_int, _S]),
     ("nrm_backward", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, _S]),

@@ -16,6 +16,7 @@
 #include <cstring>
 #include <fstream>
 #include <map>
+#include <mutex>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -134,7 +135,7 @@ int pow2_align(uintptr_t v, int cap) {
 // for the kernel that will read it. Returns NRM_OK or an error (message set).
 int make_desc(FrameDesc* d, const void* depth, void* normals, uint8_t* valid, int H, int W,
               long long depth_pitch, long long out_pitch, const nrm_intrinsics& K, int in_dtype,
-              const nrm_params& p, int tile_x, int tile_y, int box_w, int box_h) {
+              const nrm_params& p, int tile_x, int tile_y, int box_w, int box_h, float* points = nullptr) {
   std::memset(d, 0, sizeof(*d));
   d->depth = depth;
   d->normals = normals;
@@ -154,6 +155,8 @@ int make_desc(FrameDesc* d, const void* depth, void* normals, uint8_t* valid, in
   d->cx = (float)K.cx;
   d->cy = (float)K.cy;
   d->in_dtype = in_dtype;
+  d->points = points;
+  d->point_scale = (float)s;
   d->mask_align = valid ? std::min(pow2_align((uintptr_t)valid, 16), pow2_align((uintptr_t)out_pitch, 16)) : 1;
   const int eb = in_dtype == NRM_IN_U16_MM ? 2 : 4;
   const bool aligned = ((uintptr_t)depth % 16 == 0) && ((depth_pitch * eb) % 16 == 0) &&
@@ -216,6 +219,7 @@ struct Slot {
   cudaGraphNode_t copy_node = nullptr;
   cudaEvent_t ev_start = nullptr, ev_end = nullptr, done = nullptr;
   bool graph_timed = false;
+  bool graph_points = false;  // the graph's kernel also writes point clouds
   bool in_flight = false;
   bool timed_launch = false;
   int tiles = 0;
@@ -242,6 +246,9 @@ struct nrm_handle {
   nrm_tile_config cfg = {128, 16, 256, 3, 0};
   const FwdKernelSet* ks = nullptr;
   int persistent_grid = 0;
+  const void* pts_plain = nullptr;       // the configuration's kernels that also write
+  const void* pts_persistent = nullptr;  // point clouds (out dtype of p)
+  int persistent_grid_pts = 0;
   int* d_status = nullptr;
   unsigned long long timeout_ns = kDefaultTimeoutNs;
   Slot slots[kSlots];
@@ -282,6 +289,8 @@ struct DeviceGuard {
 int set_smem_attr(const void* fn, unsigned bytes) {
   // Per (kernel, device) maximum already granted.
   static std::map<std::pair<const void*, int>, unsigned> granted;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
   int dev = 0;
   cudaGetDevice(&dev);
   auto key = std::make_pair(fn, dev);
@@ -339,16 +348,26 @@ int configure(nrm_handle* h, const nrm_tile_config& c) {
   const int out = h->p.out_dtype;
   const unsigned ps = nrm::persistent_smem_bytes(c.tile_x, c.tile_y, h->p.alpha, c.stages);
   const unsigned pl = nrm::plain_smem_bytes(c.tile_x, c.tile_y, h->p.alpha);
+  const void* pts_pers = nrm::fwd_points_kernel(c.tile_x, c.tile_y, c.threads, out, true);
+  const void* pts_plain = nrm::fwd_points_kernel(c.tile_x, c.tile_y, c.threads, out, false);
+  if (!pts_pers || !pts_plain) return fail(NRM_ERR_UNSUPPORTED, "no point-cloud kernel for this configuration");
   int rc = set_smem_attr(ks->persistent[out], ps);
   if (rc) return rc;
   rc = set_smem_attr(ks->plain[out], pl);
   if (rc) return rc;
-  int occ = 0;
+  rc = set_smem_attr(pts_pers, ps);
+  if (rc) return rc;
+  rc = set_smem_attr(pts_plain, pl);
+  if (rc) return rc;
+  int occ = 0, occ_pts = 0;
   NRM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks->persistent[out],
                                                          nrm::persistent_threads(c.threads), ps),
            "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-  if (occ < 1) return fail(NRM_ERR_UNSUPPORTED, "persistent kernel does not fit on an SM");
+  NRM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_pts, pts_pers, nrm::persistent_threads(c.threads), ps),
+           "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (occ < 1 || occ_pts < 1) return fail(NRM_ERR_UNSUPPORTED, "persistent kernel does not fit on an SM");
   const int per_sm = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, occ) : occ;
+  const int per_sm_pts = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, occ_pts) : occ_pts;
   // Retire work that used the old graphs before replacing them.
   rc = retire_all(h);
   if (rc) return rc;
@@ -356,11 +375,15 @@ int configure(nrm_handle* h, const nrm_tile_config& c) {
   h->cfg = c;
   h->ks = ks;
   h->persistent_grid = per_sm * h->sm_count;
+  h->pts_plain = pts_plain;
+  h->pts_persistent = pts_pers;
+  h->persistent_grid_pts = per_sm_pts * h->sm_count;
   return NRM_OK;
 }
 
-// (Re)builds a slot's graph: upload node -> [ev_start] -> kernel -> [ev_end].
-int build_slot_graph(nrm_handle* h, Slot& s) {
+// (Re)builds a slot's graph: upload node -> [ev_start] -> kernel -> [ev_end];
+// with points, the kernel variant that also writes point clouds.
+int build_slot_graph(nrm_handle* h, Slot& s, bool points) {
   destroy_slot_graph(s);
   NRM_CUDA(cudaGraphCreate(&s.graph, 0), "cudaGraphCreate");
   NRM_CUDA(cudaGraphAddMemcpyNode1D(&s.copy_node, s.graph, nullptr, 0, s.dev, s.host,
@@ -382,8 +405,8 @@ int build_slot_graph(nrm_handle* h, Slot& s) {
   void* kargs[2] = {&args, &g};
   cudaKernelNodeParams kp;
   std::memset(&kp, 0, sizeof(kp));
-  kp.func = const_cast<void*>(h->ks->persistent[h->p.out_dtype]);
-  kp.gridDim = dim3(h->persistent_grid);
+  kp.func = const_cast<void*>(points ? h->pts_persistent : h->ks->persistent[h->p.out_dtype]);
+  kp.gridDim = dim3(points ? h->persistent_grid_pts : h->persistent_grid);
   kp.blockDim = dim3(nrm::persistent_threads(h->cfg.threads));
   kp.sharedMemBytes = nrm::persistent_smem_bytes(h->cfg.tile_x, h->cfg.tile_y, h->p.alpha, h->cfg.stages);
   kp.kernelParams = kargs;
@@ -395,6 +418,7 @@ int build_slot_graph(nrm_handle* h, Slot& s) {
   }
   NRM_CUDA(cudaGraphInstantiate(&s.exec, s.graph, 0), "cudaGraphInstantiate");
   s.graph_timed = h->timing;
+  s.graph_points = points;
   return NRM_OK;
 }
 
@@ -427,6 +451,7 @@ int validate_frame(const nrm_frame& f, int i, int out_dtype) {
   if ((uintptr_t)f.normals % na) return fail(NRM_ERR_INVALID_ARG, "frame %d: normals not %d-byte aligned", i, (int)na);
   const int eb = f.in_dtype == NRM_IN_U16_MM ? 2 : 4;
   if ((uintptr_t)f.depth % eb) return fail(NRM_ERR_INVALID_ARG, "frame %d: depth not %d-byte aligned", i, eb);
+  if ((uintptr_t)f.points % 16) return fail(NRM_ERR_INVALID_ARG, "frame %d: points not 16-byte aligned", i);
   if (f.H > (1 << 24) || f.W > (1 << 24)) return fail(NRM_ERR_UNSUPPORTED, "frame %d: dimension above 2^24", i);
   return validate_intrinsics(f.K) ? fail(NRM_ERR_INVALID_ARG, "frame %d: bad intrinsics", i) : NRM_OK;
 }
@@ -501,7 +526,7 @@ int host_validate_frame(const nrm_frame& f, int index, int out_dtype) { return v
 void host_make_forward_desc(FrameDesc* d, const nrm_frame& f, const nrm_params& p, int tile_x, int tile_y) {
   const int eb = f.in_dtype == NRM_IN_U16_MM ? 2 : 4;
   make_desc(d, f.depth, f.normals, f.valid, f.H, f.W, f.depth_pitch, f.out_pitch, f.K, f.in_dtype, p, tile_x,
-            tile_y, tile_x + 2 * pad_x(p.alpha, eb), tile_y + 2 * p.alpha);
+            tile_y, tile_x + 2 * pad_x(p.alpha, eb), tile_y + 2 * p.alpha, f.points);
 }
 
 }  // namespace nrm
@@ -635,11 +660,12 @@ void nrm_destroy(nrm_handle* h) {
   delete h;
 }
 
-int nrm_estimate(nrm_handle* h, const void* depth, void* normals, uint8_t* valid, void* cuda_stream) {
+static int estimate_single(nrm_handle* h, const void* depth, void* normals, uint8_t* valid, float* points,
+                           void* cuda_stream) {
   g_last_error.clear();
   if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
   if (h->H == 0 || h->W == 0) return fail(NRM_ERR_INVALID_ARG, "handle was created for batched calls only");
-  nrm_frame f;
+  nrm_frame f = {};
   f.depth = depth;
   f.normals = normals;
   f.valid = valid;
@@ -649,6 +675,7 @@ int nrm_estimate(nrm_handle* h, const void* depth, void* normals, uint8_t* valid
   f.out_pitch = h->W;
   f.K = h->K;
   f.in_dtype = h->p.in_dtype;
+  f.points = points;
   int rc = validate_frame(f, 0, h->p.out_dtype);
   if (rc) return rc;
   DeviceGuard guard(h->device);
@@ -656,17 +683,30 @@ int nrm_estimate(nrm_handle* h, const void* depth, void* normals, uint8_t* valid
   const int eb = f.in_dtype == NRM_IN_U16_MM ? 2 : 4;
   FrameDesc d;
   make_desc(&d, depth, normals, valid, f.H, f.W, f.depth_pitch, f.out_pitch, f.K, f.in_dtype, h->p, TX, TY,
-            TX + 2 * nrm::pad_x(h->p.alpha, eb), TY + 2 * h->p.alpha);
+            TX + 2 * nrm::pad_x(h->p.alpha, eb), TY + 2 * h->p.alpha, points);
   nrm::Globals g = make_globals(h);
   dim3 grid((f.W + TX - 1) / TX, (f.H + TY - 1) / TY);
   if (grid.y > 65535) return fail(NRM_ERR_UNSUPPORTED, "too many tile rows for a plain launch");
   void* args[2] = {&d, &g};
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  NRM_CUDA(cudaLaunchKernel(h->ks->plain[h->p.out_dtype], grid, dim3(h->cfg.threads), args,
-                            nrm::plain_smem_bytes(TX, TY, h->p.alpha), st),
+  NRM_CUDA(cudaLaunchKernel(points ? h->pts_plain : h->ks->plain[h->p.out_dtype], grid, dim3(h->cfg.threads),
+                            args, nrm::plain_smem_bytes(TX, TY, h->p.alpha), st),
            "launch fwd_plain_kernel");
   NRM_CUDA(cudaEventRecord(h->last_single, st), "cudaEventRecord");
   return NRM_OK;
+}
+
+int nrm_estimate(nrm_handle* h, const void* depth, void* normals, uint8_t* valid, void* cuda_stream) {
+  return estimate_single(h, depth, normals, valid, nullptr, cuda_stream);
+}
+
+int nrm_estimate_points(nrm_handle* h, const void* depth, void* normals, uint8_t* valid, float* points,
+                        void* cuda_stream) {
+  if (!points) {
+    g_last_error.clear();
+    return fail(NRM_ERR_INVALID_ARG, "points is NULL");
+  }
+  return estimate_single(h, depth, normals, valid, points, cuda_stream);
 }
 
 int nrm_estimate_batched(nrm_handle* h, const nrm_frame* frames, int n, void* cuda_stream) {
@@ -698,11 +738,13 @@ int nrm_estimate_batched(nrm_handle* h, const nrm_frame* frames, int n, void* cu
   int* tb = reinterpret_cast<int*>(base + nrm::kTileBeginOffset);
   FrameDesc* fd = reinterpret_cast<FrameDesc*>(base + nrm::frames_offset(s.capacity));
   int acc = 0;
+  bool points = false;
   for (int i = 0; i < n; ++i) {
     const nrm_frame& f = frames[i];
+    points = points || (f.points && (long long)f.H * f.W > 0);
     const int eb = f.in_dtype == NRM_IN_U16_MM ? 2 : 4;
     make_desc(&fd[i], f.depth, f.normals, f.valid, f.H, f.W, f.depth_pitch, f.out_pitch, f.K, f.in_dtype, h->p,
-              TX, TY, TX + 2 * nrm::pad_x(h->p.alpha, eb), TY + 2 * h->p.alpha);
+              TX, TY, TX + 2 * nrm::pad_x(h->p.alpha, eb), TY + 2 * h->p.alpha, f.points);
     fd[i].tile_begin = acc;
     tb[i] = acc;
     acc += fd[i].tiles_x * ((f.H + TY - 1) / TY);
@@ -710,8 +752,8 @@ int nrm_estimate_batched(nrm_handle* h, const nrm_frame* frames, int n, void* cu
   tb[n] = acc;
   hdr->n_frames = n;
   hdr->total_tiles = acc;
-  if (!s.exec || s.graph_timed != h->timing) {
-    rc = build_slot_graph(h, s);
+  if (!s.exec || s.graph_timed != h->timing || s.graph_points != points) {
+    rc = build_slot_graph(h, s, points);
     if (rc) return rc;
   }
   // Upload only the used part: header + tile_begin, and the used descriptors.
@@ -889,7 +931,7 @@ int nrm_estimate_multiscale(nrm_handle* h, const void* depth, void* normals, uin
     ms.alpha[i] = a;
     ms.alpha_max = std::max(ms.alpha_max, a);
   }
-  nrm_frame f;
+  nrm_frame f = {};
   f.depth = depth;
   f.normals = normals;
   f.valid = valid;
@@ -936,7 +978,7 @@ int nrm_plane_fit(nrm_handle* h, const void* depth, float* normals, uint8_t* val
   if (h->H == 0 || h->W == 0) return fail(NRM_ERR_INVALID_ARG, "handle was created for batched calls only");
   if (radius < 1 || radius > NRM_MAX_PLANE_RADIUS)
     return fail(NRM_ERR_UNSUPPORTED, "radius %d outside 1..%d", radius, NRM_MAX_PLANE_RADIUS);
-  nrm_frame f;
+  nrm_frame f = {};
   f.depth = depth;
   f.normals = normals;
   f.valid = valid;

@@ -221,6 +221,8 @@ struct TileFrame {
   uint8_t* valid;
   const void* depth;
   long long depth_pitch;
+  float* points;       // optional point cloud output, or NULL
+  float point_scale;   // metres per decoded depth unit
 };
 
 __device__ __forceinline__ TileFrame tile_frame(const FrameDesc& fd, float sign) {
@@ -241,6 +243,8 @@ __device__ __forceinline__ TileFrame tile_frame(const FrameDesc& fd, float sign)
   f.valid = fd.valid;
   f.depth = fd.depth;
   f.depth_pitch = fd.depth_pitch;
+  f.points = fd.points;
+  f.point_scale = fd.point_scale;
   return f;
 }
 
@@ -446,7 +450,7 @@ struct QuadStencil {
 // of the scalar operations. Per-column terms are computed once per tile. Mask
 // bytes are gathered with one ballot per 32 pixels and written as TX/32
 // consecutive bytes per lane.
-template <int TX, int TY, int NT, int OUT, bool SECANT, bool FULL, class Stencil>
+template <int TX, int TY, int NT, int OUT, bool SECANT, bool FULL, class Stencil, bool POINTS = false>
 __device__ __forceinline__ void compute_tile_with(const float* __restrict__ F, int bw, int padx,
                                                   const TileFrame& f, int gx0, int gy0, int halo, float tau2,
                                                   const Stencil& st) {
@@ -560,34 +564,55 @@ __device__ __forceinline__ void compute_tile_with(const float* __restrict__ F, i
       }
     }
   }
+  if (POINTS && f.points) {
+    // Organised point cloud P = d1 (u1, v1, 1) in metres (Section 2), the
+    // origin where d1 is invalid (independent of the normal mask): a second
+    // pass over the decoded tile, compiled only into the kernels instantiated
+    // with POINTS (they need more registers than the normal-only kernels).
+#pragma unroll 1
+    for (int ly = warp; ly < TY; ly += NW) {
+      const int gy = gy0 + ly;
+      if (gy >= f.H) break;
+      const float v1 = ((float)gy - f.cy) * f.inv_fy;
+      const float* row = F + (ly + halo) * bw + padx + lane;
+      float4* prow = reinterpret_cast<float4*>(f.points) + (long long)gy * f.out_pitch + gx0 + lane;
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const float d = row[32 * c];
+        const float z = d * f.point_scale;
+        const float u1 = (c & 1) ? -nu1[c >> 1].y : -nu1[c >> 1].x;
+        const float4 q = d == d ? make_float4(z * u1, z * v1, z, 0.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (FULL || colok[c]) __stcs(prow + 32 * c, q);
+      }
+    }
+  }
 }
 
-
-template <int TX, int TY, int NT, int OUT, bool SECANT, bool FULL>
+template <int TX, int TY, int NT, int OUT, bool SECANT, bool FULL, bool POINTS>
 __device__ __forceinline__ void compute_tile(const float* __restrict__ F, int bw, int padx,
                                              const TileFrame& f, int gx0, int gy0, int alpha,
                                              float tau2) {
   const QuadStencil st{f2(f.a, f.a), f2(f.b, f.b), f2(f.c, f.c), alpha, alpha * bw};
-  compute_tile_with<TX, TY, NT, OUT, SECANT, FULL>(F, bw, padx, f, gx0, gy0, alpha, tau2, st);
+  compute_tile_with<TX, TY, NT, OUT, SECANT, FULL, QuadStencil, POINTS>(F, bw, padx, f, gx0, gy0, alpha, tau2, st);
 }
 
 // compute_tile for the tile's mask mode, with the column checks compiled out
 // for tiles that lie entirely inside the image width (all but the last tile
 // column of a frame whose width is not a multiple of TX).
-template <int TX, int TY, int NT, int OUT>
+template <int TX, int TY, int NT, int OUT, bool POINTS>
 __device__ __forceinline__ void compute_tile_any(const float* __restrict__ F, int bw, int padx,
                                                  const TileFrame& f, int gx0, int gy0, const Globals& g) {
   const bool full = gx0 + TX <= f.W;
   if (g.mask_mode == NRM_MASK_SECANT) {
     if (full)
-      compute_tile<TX, TY, NT, OUT, true, true>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
+      compute_tile<TX, TY, NT, OUT, true, true, POINTS>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
     else
-      compute_tile<TX, TY, NT, OUT, true, false>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
+      compute_tile<TX, TY, NT, OUT, true, false, POINTS>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
   } else {
     if (full)
-      compute_tile<TX, TY, NT, OUT, false, true>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
+      compute_tile<TX, TY, NT, OUT, false, true, POINTS>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
     else
-      compute_tile<TX, TY, NT, OUT, false, false>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
+      compute_tile<TX, TY, NT, OUT, false, false, POINTS>(F, bw, padx, f, gx0, gy0, g.alpha, g.tau2);
   }
 }
 

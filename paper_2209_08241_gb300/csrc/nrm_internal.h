@@ -43,7 +43,8 @@ struct alignas(128) FrameDesc {
   int in_dtype;            // NRM_IN_F32_M or NRM_IN_U16_MM
   int use_tma;             // 1: TMA tile loads; 0: plain loads (unaligned base or pitch)
   int mask_align;          // bytes: largest power of two (<= 16) dividing mask base and pitch
-  int pad_;
+  float point_scale;       // metres per decoded depth unit (u16: depth_scale; f32: 1)
+  float* points;           // optional organised point cloud (x, y, z, 0) per pixel, pitch out_pitch; or NULL
 };
 static_assert(sizeof(FrameDesc) == 256, "FrameDesc layout");
 
@@ -87,10 +88,13 @@ struct FwdKernelSet {
   const void* persistent[3];  // [out_dtype] fwd_persistent_kernel<...>
 };
 
-// All compiled forward configurations (nrm_forward_*.cu).
+// All compiled forward configurations (nrm_forward.cu).
 int fwd_kernel_count();
 const FwdKernelSet* fwd_kernel(int i);
 const FwdKernelSet* fwd_kernel_find(int tile_x, int tile_y, int threads);
+// The same configuration's kernel that also writes the point cloud
+// (nrm_forward_points.cu), or NULL.
+const void* fwd_points_kernel(int tile_x, int tile_y, int threads, int out_dtype, bool persistent);
 
 // Stage buffer bytes for a tile config and alpha (max over input dtypes).
 NRM_HD inline unsigned stage_bytes_for(int tile_x, int tile_y, int alpha) {

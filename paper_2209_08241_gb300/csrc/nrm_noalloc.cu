@@ -87,6 +87,8 @@ extern "C" int nrm_estimate_batched_noalloc(const nrm_frame* frames, int n, cons
   for (int i = 0; i < n; ++i) {
     rc = nrm::host_validate_frame(frames[i], i, p.out_dtype);
     if (rc) return rc;
+    if (frames[i].points)
+      return nrm::host_fail(NRM_ERR_UNSUPPORTED, "nrm_estimate_batched_noalloc writes no point clouds");
     total += (long long)((frames[i].W + kTileX - 1) / kTileX) * ((frames[i].H + kTileY - 1) / kTileY);
   }
   if (total == 0) return NRM_OK;

@@ -48,12 +48,12 @@ def test_struct_layouts_match_c(tmp_path):
 #include <stdio.h>
 #include "nrm.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(nrm_intrinsics), sizeof(nrm_params), sizeof(nrm_frame),
-         sizeof(nrm_tile_config), sizeof(nrm_stats));
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", offsetof(nrm_frame, depth), offsetof(nrm_frame, normals),
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(nrm_intrinsics), sizeof(nrm_params), sizeof(nrm_frame),
+         sizeof(nrm_tile_config), sizeof(nrm_stats), sizeof(nrm_scales));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", offsetof(nrm_frame, depth), offsetof(nrm_frame, normals),
          offsetof(nrm_frame, valid), offsetof(nrm_frame, H), offsetof(nrm_frame, W),
          offsetof(nrm_frame, depth_pitch), offsetof(nrm_frame, out_pitch), offsetof(nrm_frame, K),
-         offsetof(nrm_frame, in_dtype));
+         offsetof(nrm_frame, in_dtype), offsetof(nrm_frame, points));
   printf("%zu %zu %zu\n", offsetof(nrm_stats, launches), offsetof(nrm_stats, kernel_ms),
          offsetof(nrm_stats, tiles));
   return 0;
@@ -64,11 +64,11 @@ int main(void) {
     lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     sizes = [int(v) for v in lines[0].split()]
     assert sizes == [ctypes.sizeof(_lib.Intrinsics), ctypes.sizeof(_lib.Params), ctypes.sizeof(_lib.Frame),
-                     ctypes.sizeof(_lib.TileConfig), ctypes.sizeof(_lib.Stats)]
+                     ctypes.sizeof(_lib.TileConfig), ctypes.sizeof(_lib.Stats), ctypes.sizeof(_lib.Scales)]
     F = _lib.Frame
     offs = [int(v) for v in lines[1].split()]
     assert offs == [F.depth.offset, F.normals.offset, F.valid.offset, F.H.offset, F.W.offset,
-                    F.depth_pitch.offset, F.out_pitch.offset, F.K.offset, F.in_dtype.offset]
+                    F.depth_pitch.offset, F.out_pitch.offset, F.K.offset, F.in_dtype.offset, F.points.offset]
     S = _lib.Stats
     assert [int(v) for v in lines[2].split()] == [S.launches.offset, S.kernel_ms.offset, S.tiles.offset]
 
