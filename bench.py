@@ -213,8 +213,8 @@ def bench_ours(args, dist: Dist):
     px_per_step = N_FRAMES * H_FULLHD * W_FULLHD
     stream = torch.cuda.current_stream(dev)
     if args.config:
-        tx, ty, nt, st = (int(v) for v in args.config.split(","))
-        est.set_config(tx, ty, nt, st)
+        vals = [int(v) for v in args.config.split(",")]
+        est.set_config(*vals)
     elif not args.no_autotune:
         # Tile shape, threads and pipeline depth for this workload (timed here;
         # the library caches nothing between fresh processes without a path).
@@ -327,7 +327,9 @@ def bench_ours(args, dist: Dist):
                    "frames_per_gpu": N_FRAMES, "H": H_FULLHD, "W": W_FULLHD, "alpha": 2,
                    "mask": "secant tau=12", "compute": "fp32", "out": "f32x4",
                    "tile": f"{tile['tile_x']}x{tile['tile_y']}, {tile['threads']}+32 threads, "
-                           f"{tile['stages']} stages" + ("" if (args.no_autotune or args.config) else " (autotuned)"),
+                           f"{tile['stages']} stages"
+                           + (f", {tile['ctas_per_sm']} CTAs/SM" if tile.get("ctas_per_sm") else "")
+                           + ("" if (args.no_autotune or args.config) else " (autotuned)"),
                    "parallelism": f"frame-sharded x{dist.world} (no collective)",
                    "l2": f"inputs larger than L2 ({px_per_step * BYTES_PER_PX / 1e6:.0f} MB moved per step)"},
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
@@ -512,11 +514,13 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
     dfr, _ = db.make_frames(items, [(nbuf[i], vbuf[i]) for i in range(Nd)])
     glist, vlist, dlist = [gbuf[i] for i in range(Nd)], [vbuf[i] for i in range(Nd)], [grad[i] for i in range(Nd)]
 
+    gfr, _ = db.make_grad_frames(items, glist, vlist, dlist)
+
     def fwd_bwd():
         db.run(dfr, Nd, stream)
         cnt = vbuf.sum(dim=(1, 2), keepdim=True).clamp(min=1).float()
         gbuf[..., :3] = -tg * (vbuf.unsqueeze(-1).float() / cnt.unsqueeze(-1))
-        db.backward(items, glist, vlist, dlist, stream)
+        db.run_backward(gfr, Nd, stream)
 
     for _ in range(3):
         fwd_bwd()
@@ -530,7 +534,7 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
     out["diff32_fwd_bwd_mpx_s"] = round(Nd * Hd * Wd / (ms / 1e3) / 1e6, 1)
     e0.record(stream)
     for _ in range(reps):
-        db.backward(items, glist, vlist, dlist, stream)
+        db.run_backward(gfr, Nd, stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / reps
@@ -733,7 +737,7 @@ def main(argv=None):
     ap.add_argument("--frames", type=int, default=N_FRAMES,
                     help="frames per GPU (default 64; smaller only for profiling)")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--config", default="", help="tile_x,tile_y,threads,stages (skips the autotuner)")
+    ap.add_argument("--config", default="", help="tile_x,tile_y,threads,stages[,ctas_per_sm] (skips the autotuner)")
     ap.add_argument("--skip-extra", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")

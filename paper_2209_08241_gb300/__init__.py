@@ -372,11 +372,12 @@ class BatchedEstimator(_Handle):
             valid_host.copy_(staging["valid"], non_blocking=True)
         return staging
 
-    def backward(self, items: Sequence, grad_normals: Sequence, valids: Sequence,
-                 grad_depths: Sequence | None = None, stream=None) -> list:
-        """Adjoint of a batch in one launch: items [(depth float32 (H, W), K)],
+    def make_grad_frames(self, items: Sequence, grad_normals: Sequence, valids: Sequence,
+                         grad_depths: Sequence | None = None):
+        """ctypes adjoint frame array for items [(depth float32 (H, W), K)],
         grad_normals [(H, W, 4) float32], valids [(H, W) uint8 masks from the
-        forward]; returns (or fills) [(H, W) float32] depth gradients."""
+        forward] and depth gradients [(H, W) float32] (allocated when None).
+        Returns (frames_array, grad_depths)."""
         n = len(items)
         arr = (_lib.GradFrame * max(n, 1))()
         outs = []
@@ -403,7 +404,18 @@ class BatchedEstimator(_Handle):
             f.out_pitch = int(g.stride(0) // 4) if depth.numel() else f.W
             f.K = _intr(K)
             outs.append(gd)
-        _lib.check(self.lib.nrm_backward_batched(self.h, arr, n, _stream_ptr(stream)), "nrm_backward_batched")
+        return arr, outs
+
+    def run_backward(self, grad_frames_array, n: int, stream=None):
+        _lib.check(self.lib.nrm_backward_batched(self.h, grad_frames_array, int(n), _stream_ptr(stream)),
+                   "nrm_backward_batched")
+
+    def backward(self, items: Sequence, grad_normals: Sequence, valids: Sequence,
+                 grad_depths: Sequence | None = None, stream=None) -> list:
+        """Adjoint of a batch in one launch (see ``make_grad_frames``); returns
+        (or fills) the [(H, W) float32] depth gradients."""
+        arr, outs = self.make_grad_frames(items, grad_normals, valids, grad_depths)
+        self.run_backward(arr, len(items), stream)
         return outs
 
     def autotune(self, items: Sequence, outputs: Sequence | None = None, cache_path: str | None = None,

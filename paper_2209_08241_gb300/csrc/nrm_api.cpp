@@ -220,6 +220,7 @@ struct Slot {
   cudaEvent_t ev_start = nullptr, ev_end = nullptr, done = nullptr;
   bool graph_timed = false;
   bool graph_points = false;  // the graph's kernel also writes point clouds
+  bool graph_u16 = false;     // the graph's staging buffers are sized for uint16 frames only
   bool in_flight = false;
   bool timed_launch = false;
   int tiles = 0;
@@ -245,10 +246,12 @@ struct nrm_handle {
   nrm_params p;
   nrm_tile_config cfg = {128, 16, 256, 3, 0};
   const FwdKernelSet* ks = nullptr;
-  int persistent_grid = 0;
+  // Persistent grids [u16]: u16 = 1 for batches of uint16 frames only, whose
+  // smaller staging buffers let more CTAs share an SM.
+  int persistent_grid[2] = {0, 0};
   const void* pts_plain = nullptr;       // the configuration's kernels that also write
   const void* pts_persistent = nullptr;  // point clouds (out dtype of p)
-  int persistent_grid_pts = 0;
+  int persistent_grid_pts[2] = {0, 0};
   int* d_status = nullptr;
   unsigned long long timeout_ns = kDefaultTimeoutNs;
   Slot slots[kSlots];
@@ -359,31 +362,37 @@ int configure(nrm_handle* h, const nrm_tile_config& c) {
   if (rc) return rc;
   rc = set_smem_attr(pts_plain, pl);
   if (rc) return rc;
-  int occ = 0, occ_pts = 0;
-  NRM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks->persistent[out],
-                                                         nrm::persistent_threads(c.threads), ps),
-           "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-  NRM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_pts, pts_pers, nrm::persistent_threads(c.threads), ps),
-           "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-  if (occ < 1 || occ_pts < 1) return fail(NRM_ERR_UNSUPPORTED, "persistent kernel does not fit on an SM");
-  const int per_sm = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, occ) : occ;
-  const int per_sm_pts = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, occ_pts) : occ_pts;
+  // CTAs per SM for each kernel and staging size (any dtype / uint16 only).
+  int per_sm[2][2];  // [points][u16]
+  const void* pk[2] = {ks->persistent[out], pts_pers};
+  for (int k = 0; k < 2; ++k)
+    for (int u = 0; u < 2; ++u) {
+      const unsigned bytes = nrm::persistent_smem_bytes(c.tile_x, c.tile_y, h->p.alpha, c.stages, u ? 2 : 0);
+      int occ = 0;
+      NRM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pk[k], nrm::persistent_threads(c.threads), bytes),
+               "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+      if (occ < 1) return fail(NRM_ERR_UNSUPPORTED, "persistent kernel does not fit on an SM");
+      per_sm[k][u] = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, occ) : occ;
+    }
   // Retire work that used the old graphs before replacing them.
   rc = retire_all(h);
   if (rc) return rc;
   for (auto& s : h->slots) destroy_slot_graph(s);
   h->cfg = c;
   h->ks = ks;
-  h->persistent_grid = per_sm * h->sm_count;
+  for (int u = 0; u < 2; ++u) {
+    h->persistent_grid[u] = per_sm[0][u] * h->sm_count;
+    h->persistent_grid_pts[u] = per_sm[1][u] * h->sm_count;
+  }
   h->pts_plain = pts_plain;
   h->pts_persistent = pts_pers;
-  h->persistent_grid_pts = per_sm_pts * h->sm_count;
   return NRM_OK;
 }
 
 // (Re)builds a slot's graph: upload node -> [ev_start] -> kernel -> [ev_end];
-// with points, the kernel variant that also writes point clouds.
-int build_slot_graph(nrm_handle* h, Slot& s, bool points) {
+// with points, the kernel variant that also writes point clouds; with u16,
+// staging buffers sized for uint16 frames (and the larger grid that allows).
+int build_slot_graph(nrm_handle* h, Slot& s, bool points, bool u16) {
   destroy_slot_graph(s);
   NRM_CUDA(cudaGraphCreate(&s.graph, 0), "cudaGraphCreate");
   NRM_CUDA(cudaGraphAddMemcpyNode1D(&s.copy_node, s.graph, nullptr, 0, s.dev, s.host,
@@ -400,15 +409,15 @@ int build_slot_graph(nrm_handle* h, Slot& s, bool points) {
   args.tile_begin = reinterpret_cast<const int*>(static_cast<char*>(s.dev) + nrm::kTileBeginOffset);
   args.frames = reinterpret_cast<const FrameDesc*>(static_cast<char*>(s.dev) + nrm::frames_offset(s.capacity));
   args.stages = h->cfg.stages;
-  args.stage_bytes = nrm::stage_bytes_for(h->cfg.tile_x, h->cfg.tile_y, h->p.alpha);
+  args.stage_bytes = nrm::stage_bytes_for(h->cfg.tile_x, h->cfg.tile_y, h->p.alpha, u16 ? 2 : 0);
   nrm::Globals g = make_globals(h);
   void* kargs[2] = {&args, &g};
   cudaKernelNodeParams kp;
   std::memset(&kp, 0, sizeof(kp));
   kp.func = const_cast<void*>(points ? h->pts_persistent : h->ks->persistent[h->p.out_dtype]);
-  kp.gridDim = dim3(points ? h->persistent_grid_pts : h->persistent_grid);
+  kp.gridDim = dim3(points ? h->persistent_grid_pts[u16] : h->persistent_grid[u16]);
   kp.blockDim = dim3(nrm::persistent_threads(h->cfg.threads));
-  kp.sharedMemBytes = nrm::persistent_smem_bytes(h->cfg.tile_x, h->cfg.tile_y, h->p.alpha, h->cfg.stages);
+  kp.sharedMemBytes = nrm::persistent_smem_bytes(h->cfg.tile_x, h->cfg.tile_y, h->p.alpha, h->cfg.stages, u16 ? 2 : 0);
   kp.kernelParams = kargs;
   cudaGraphNode_t kn;
   NRM_CUDA(cudaGraphAddKernelNode(&kn, s.graph, &prev, 1, &kp), "cudaGraphAddKernelNode");
@@ -419,6 +428,7 @@ int build_slot_graph(nrm_handle* h, Slot& s, bool points) {
   NRM_CUDA(cudaGraphInstantiate(&s.exec, s.graph, 0), "cudaGraphInstantiate");
   s.graph_timed = h->timing;
   s.graph_points = points;
+  s.graph_u16 = u16;
   return NRM_OK;
 }
 
@@ -738,10 +748,11 @@ int nrm_estimate_batched(nrm_handle* h, const nrm_frame* frames, int n, void* cu
   int* tb = reinterpret_cast<int*>(base + nrm::kTileBeginOffset);
   FrameDesc* fd = reinterpret_cast<FrameDesc*>(base + nrm::frames_offset(s.capacity));
   int acc = 0;
-  bool points = false;
+  bool points = false, u16 = true;
   for (int i = 0; i < n; ++i) {
     const nrm_frame& f = frames[i];
     points = points || (f.points && (long long)f.H * f.W > 0);
+    u16 = u16 && (f.in_dtype == NRM_IN_U16_MM || (long long)f.H * f.W == 0);
     const int eb = f.in_dtype == NRM_IN_U16_MM ? 2 : 4;
     make_desc(&fd[i], f.depth, f.normals, f.valid, f.H, f.W, f.depth_pitch, f.out_pitch, f.K, f.in_dtype, h->p,
               TX, TY, TX + 2 * nrm::pad_x(h->p.alpha, eb), TY + 2 * h->p.alpha, f.points);
@@ -752,8 +763,8 @@ int nrm_estimate_batched(nrm_handle* h, const nrm_frame* frames, int n, void* cu
   tb[n] = acc;
   hdr->n_frames = n;
   hdr->total_tiles = acc;
-  if (!s.exec || s.graph_timed != h->timing || s.graph_points != points) {
-    rc = build_slot_graph(h, s, points);
+  if (!s.exec || s.graph_timed != h->timing || s.graph_points != points || s.graph_u16 != u16) {
+    rc = build_slot_graph(h, s, points, u16);
     if (rc) return rc;
   }
   // Upload only the used part: header + tile_begin, and the used descriptors.
@@ -1088,11 +1099,33 @@ int nrm_autotune(nrm_handle* h, const nrm_frame* frames, int n, void* cuda_strea
   nrm_tile_config best = start;
   float best_ms = INFINITY;
   int rc = NRM_OK;
-  for (int i = 0; i < nrm::fwd_kernel_count() && rc == NRM_OK; ++i) {
+  // The batch decides which staging size (and so which occupancy) applies.
+  bool points = false, u16 = true;
+  for (int i = 0; i < n; ++i) {
+    points = points || frames[i].points;
+    u16 = u16 && (frames[i].in_dtype == NRM_IN_U16_MM || (long long)frames[i].H * frames[i].W == 0);
+  }
+  // Candidates: every compiled tile shape x pipeline depth x CTAs per SM from
+  // 2 up to the occupancy limit (fewer concurrent CTAs can write to HBM
+  // faster, so the limit is not always best).
+  std::vector<nrm_tile_config> cands;
+  for (int i = 0; i < nrm::fwd_kernel_count(); ++i) {
     const FwdKernelSet* k = nrm::fwd_kernel(i);
     for (int stages = 2; stages <= 4; ++stages) {
       nrm_tile_config c = {k->tile_x, k->tile_y, k->threads, stages, 0};
       if (configure(h, c) != NRM_OK) continue;  // e.g. does not fit
+      const int grid = points ? h->persistent_grid_pts[u16] : h->persistent_grid[u16];
+      const int occ = h->sm_count > 0 ? grid / h->sm_count : 1;
+      for (int ctas = std::min(2, occ); ctas <= occ; ++ctas) {
+        c.ctas_per_sm = ctas;
+        cands.push_back(c);
+      }
+    }
+  }
+  for (size_t ci = 0; ci < cands.size() && rc == NRM_OK; ++ci) {
+    {
+      const nrm_tile_config c = cands[ci];
+      if (configure(h, c) != NRM_OK) continue;
       for (int w = 0; w < 2 && rc == NRM_OK; ++w) rc = nrm_estimate_batched(h, frames, n, cuda_stream);
       if (rc) break;
       const int reps = 5;

@@ -96,11 +96,12 @@ const FwdKernelSet* fwd_kernel_find(int tile_x, int tile_y, int threads);
 // (nrm_forward_points.cu), or NULL.
 const void* fwd_points_kernel(int tile_x, int tile_y, int threads, int out_dtype, bool persistent);
 
-// Stage buffer bytes for a tile config and alpha (max over input dtypes).
-NRM_HD inline unsigned stage_bytes_for(int tile_x, int tile_y, int alpha) {
+// Stage buffer bytes for a tile config and alpha: for input elements of eb
+// bytes (2: uint16, 4: float32), or the maximum over both (eb = 0).
+NRM_HD inline unsigned stage_bytes_for(int tile_x, int tile_y, int alpha, int eb = 0) {
   unsigned f32 = (unsigned)((tile_x + 2 * pad_x(alpha, 4)) * (tile_y + 2 * alpha) * 4);
   unsigned u16 = (unsigned)((tile_x + 2 * pad_x(alpha, 2)) * (tile_y + 2 * alpha) * 2);
-  unsigned m = f32 > u16 ? f32 : u16;
+  unsigned m = eb == 2 ? u16 : (eb == 4 ? f32 : (f32 > u16 ? f32 : u16));
   return (m + 127) / 128 * 128;
 }
 // Bytes of the decoded float halo tile: (TX + 2 pad_x(alpha, 4)) x (TY + 2 alpha)
@@ -116,10 +117,11 @@ NRM_HD inline unsigned plain_smem_bytes(int tile_x, int tile_y, int alpha) {
 }
 // Bytes reserved per pipeline stage for the producer's tile record.
 constexpr unsigned kStageInfoBytes = 128;
-// Dynamic shared memory of the persistent kernel: `stages` staging buffers,
-// two decoded tiles, full/empty barriers (128 B) and per-stage tile records.
-NRM_HD inline unsigned persistent_smem_bytes(int tile_x, int tile_y, int alpha, int stages) {
-  return stage_bytes_for(tile_x, tile_y, alpha) * stages + 2 * ftile_bytes_for(tile_x, tile_y, alpha) +
+// Dynamic shared memory of the persistent kernel: `stages` staging buffers
+// (sized as stage_bytes_for with eb), two decoded tiles, full/empty barriers
+// (128 B) and per-stage tile records.
+NRM_HD inline unsigned persistent_smem_bytes(int tile_x, int tile_y, int alpha, int stages, int eb = 0) {
+  return stage_bytes_for(tile_x, tile_y, alpha, eb) * stages + 2 * ftile_bytes_for(tile_x, tile_y, alpha) +
          128 + kStageInfoBytes * stages;
 }
 // Threads of a persistent CTA: the compute threads plus one producer warp.

