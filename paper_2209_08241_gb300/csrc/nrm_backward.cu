@@ -23,6 +23,12 @@
 // gathers. Frames whose buffers cannot be TMA-mapped use plain loads into the
 // same shared-memory layout. bwd_kernel covers one frame (grid = its tiles);
 // bwd_batched_kernel covers a batch (grid = max tiles of a frame x frames).
+// Both are compiled for alpha = 1..4 as constants (shared-memory offsets and
+// loop steps become immediates) and once for any alpha.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "nrm_device.cuh"
 
 namespace nrm {
@@ -53,10 +59,13 @@ __host__ __device__ inline unsigned mask_tile_bytes(int alpha) {
 // gradient and mask tensor maps (param or global memory; used only when
 // fd.use_tma). If the bounded wait for the copies runs out, the tile records
 // NRM_ERR_TIMEOUT in the status word and writes nothing.
+// ALPHA > 0 compiles the tile for that pixel distance (offsets and loop steps
+// become constants); ALPHA = 0 takes g.alpha at run time.
+template <int ALPHA>
 __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d, const void* tmap_g,
                                          const void* tmap_m, int gx0, int gy0, const Globals& g,
                                          unsigned char* smem) {
-  const int alpha = g.alpha;
+  const int alpha = ALPHA > 0 ? ALPHA : g.alpha;
   const int p2 = pad_x(2 * alpha, 4);
   const int bw = TX + 2 * p2;       // depth tile pitch
   const int bh = TY + 4 * alpha;
@@ -173,14 +182,16 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d
   }
 }
 
+template <int ALPHA>
 __global__ void __launch_bounds__(NT)
     bwd_kernel(const __grid_constant__ FrameDesc fd, const __grid_constant__ BwdMaps maps, const Globals g) {
   extern __shared__ __align__(128) unsigned char smem[];
-  bwd_tile(fd, &fd.tmap, &maps.grad, &maps.mask, blockIdx.x * TX, blockIdx.y * TY, g, smem);
+  bwd_tile<ALPHA>(fd, &fd.tmap, &maps.grad, &maps.mask, blockIdx.x * TX, blockIdx.y * TY, g, smem);
 }
 
 // Grid (max tiles of a frame, frames): block (x, f) is tile x of frame f; frames
 // with fewer tiles leave their extra blocks idle.
+template <int ALPHA>
 __global__ void __launch_bounds__(NT) bwd_batched_kernel(const BwdBatchArgs args, const Globals g) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int f = (int)blockIdx.y;
@@ -195,18 +206,34 @@ __global__ void __launch_bounds__(NT) bwd_batched_kernel(const BwdBatchArgs args
   }
   const int ty = local / tiles_x;
   const int tx = local - ty * tiles_x;
-  bwd_tile(fd, &fd.tmap, &args.maps[f].grad, &args.maps[f].mask, tx * TX, ty * TY, g, smem);
+  bwd_tile<ALPHA>(fd, &fd.tmap, &args.maps[f].grad, &args.maps[f].mask, tx * TX, ty * TY, g, smem);
 }
 
-// Grants the dynamic shared memory a kernel needs, once per (kernel, device).
-cudaError_t set_smem(const void* fn, int which, unsigned bytes) {
-  static int granted[2][64] = {};
+// The kernel for alpha: compiled for alpha = 1..4 (constant offsets and loop
+// steps), generic above.
+const void* bwd_kernel_for(int alpha, bool batched) {
+  switch (alpha) {
+    case 1: return batched ? (const void*)bwd_batched_kernel<1> : (const void*)bwd_kernel<1>;
+    case 2: return batched ? (const void*)bwd_batched_kernel<2> : (const void*)bwd_kernel<2>;
+    case 3: return batched ? (const void*)bwd_batched_kernel<3> : (const void*)bwd_kernel<3>;
+    case 4: return batched ? (const void*)bwd_batched_kernel<4> : (const void*)bwd_kernel<4>;
+    default: return batched ? (const void*)bwd_batched_kernel<0> : (const void*)bwd_kernel<0>;
+  }
+}
+
+// Grants the dynamic shared memory a kernel needs, once per (kernel, device)
+// and size.
+cudaError_t set_smem(const void* fn, unsigned bytes) {
+  static std::map<std::pair<const void*, int>, unsigned> granted;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 63;
-  if ((int)bytes <= granted[which][dev]) return cudaSuccess;
+  auto key = std::make_pair(fn, dev);
+  auto it = granted.find(key);
+  if (it != granted.end() && it->second >= bytes) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) granted[which][dev] = (int)bytes;
+  if (e == cudaSuccess) granted[key] = bytes;
   return e;
 }
 
@@ -218,20 +245,29 @@ unsigned bwd_smem_bytes(int alpha) {
 
 cudaError_t launch_backward(const FrameDesc& fd, const BwdMaps& maps, const Globals& g, cudaStream_t stream) {
   const unsigned smem = bwd_smem_bytes(g.alpha);
-  cudaError_t e = set_smem((const void*)bwd_kernel, 0, smem);
+  const void* fn = bwd_kernel_for(g.alpha, false);
+  cudaError_t e = set_smem(fn, smem);
   if (e != cudaSuccess) return e;
   dim3 grid((fd.W + TX - 1) / TX, (fd.H + TY - 1) / TY);
-  bwd_kernel<<<grid, NT, smem, stream>>>(fd, maps, g);
-  return cudaGetLastError();
+  FrameDesc d = fd;
+  BwdMaps m = maps;
+  Globals gg = g;
+  void* args[3] = {&d, &m, &gg};
+  e = cudaLaunchKernel(fn, grid, dim3(NT), args, smem, stream);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_backward_batched(const BwdBatchArgs& args, int n_frames, int max_tiles, const Globals& g,
                                     cudaStream_t stream) {
   const unsigned smem = bwd_smem_bytes(g.alpha);
-  cudaError_t e = set_smem((const void*)bwd_batched_kernel, 1, smem);
+  const void* fn = bwd_kernel_for(g.alpha, true);
+  cudaError_t e = set_smem(fn, smem);
   if (e != cudaSuccess) return e;
-  bwd_batched_kernel<<<dim3(max_tiles, n_frames), NT, smem, stream>>>(args, g);
-  return cudaGetLastError();
+  BwdBatchArgs a = args;
+  Globals gg = g;
+  void* kargs[2] = {&a, &gg};
+  e = cudaLaunchKernel(fn, dim3(max_tiles, n_frames), dim3(NT), kargs, smem, stream);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace nrm
