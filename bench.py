@@ -609,12 +609,49 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
         ms = e0.elapsed_time(e1) / reps
         out[f"plane_fit_r{r}_4096x3072_mpx_s"] = round(4096 * 3072 / (ms / 1e3) / 1e6, 1)
     del pn, pv
+    out["accuracy_640x480"] = accuracy_report(nrm, scenes, dev)
     be.sync_status()
     db.sync_status()
     de.sync_status()
     del big, bn, bv, bg, bgrad, ph, th, ref_n, ref_v
     del fr, tg, nbuf, vbuf, gbuf, grad
     torch.cuda.empty_cache()
+    return out
+
+
+def _sig(t):
+    """[MSE theta, MSE phi, count] of an angle_mse result, to 4 significant digits."""
+    return [float(f"{float(v):.4g}") for v in t.tolist()]
+
+
+def accuracy_report(nrm, scenes, dev):
+    """Section 4's accuracy measure on the synthetic 640 x 480 scene: the MSE
+    of the I_theta and I_phi angle images (Tables 2-5) of the estimates against
+    the scene's exact surface normals, and against the plane-fitting ground
+    truth the paper uses on real data (25 neighbours). Noise-free and with
+    Kinect-style noise; [MSE theta, MSE phi, pixels]. All evaluation runs in
+    the library's kernels."""
+    import torch
+    K = scenes.CFG1_K
+    gt = scenes.cfg1_normals(dev)
+    gt_v = (gt.norm(dim=-1) > 0).to(torch.uint8).contiguous()
+    gt4 = torch.zeros((480, 640, 4), device=dev)
+    gt4[..., :3] = gt.float()
+    out = {}
+    for noise in (False, True):
+        d, _ = scenes.cfg1_depth(dev, noise=noise)
+        row = {}
+        pf = nrm.NormalEstimator(K, 480, 640, device=dev)
+        pn, pv = pf.plane_fit(d, 2)
+        for alpha in (1, 2):
+            est = nrm.NormalEstimator(K, 480, 640, nrm.NormalParams(alpha=alpha), device=dev)
+            n, m = est.estimate(d)
+            row[f"method_a{alpha}_vs_exact"] = _sig(nrm.angle_mse(est, n, m, gt4, gt_v))
+            row[f"method_a{alpha}_vs_planefit"] = _sig(nrm.angle_mse(est, n, m, pn, pv))
+            est.sync_status()
+        row["planefit_r2_vs_exact"] = _sig(nrm.angle_mse(pf, pn, pv, gt4, gt_v))
+        pf.sync_status()
+        out["noisy" if noise else "noise_free"] = row
     return out
 
 

@@ -74,6 +74,9 @@ class Plane:
         t = self.offset / den
         return torch.where((den.abs() > 1e-12) & (t > 0), t, torch.full_like(t, math.inf))
 
+    def normal_at(self, X):
+        return torch.as_tensor(self.normal, dtype=X.dtype, device=X.device).expand_as(X)
+
 
 @dataclass
 class Patch:
@@ -98,6 +101,10 @@ class Patch:
         ok = (den.abs() > 1e-12) & (t > 0) & (a.abs() <= self.h1) & (b.abs() <= self.h2)
         return torch.where(ok, t, torch.full_like(t, math.inf))
 
+    def normal_at(self, X):
+        n = np.cross(self.e1, self.e2)
+        return torch.as_tensor(n, dtype=X.dtype, device=X.device).expand_as(X)
+
 
 @dataclass
 class Sphere:
@@ -119,6 +126,9 @@ class Sphere:
         t1 = (b + sq) / a
         t = torch.where(t0 > 0, t0, t1)
         return torch.where((disc >= 0) & (t > 0), t, torch.full_like(t, math.inf))
+
+    def normal_at(self, X):
+        return (X - torch.as_tensor(self.centre, dtype=X.dtype, device=X.device)) / self.radius
 
 
 @dataclass
@@ -166,6 +176,18 @@ class Cylinder:
             best = torch.where(ok & (t < best), t, best)
         return best
 
+    def normal_at(self, X):
+        # Side: the radial direction; caps: +-axis. A point is on a cap when its
+        # height along the axis is closer to +-half_len than its radius is to R.
+        A = torch.as_tensor(self.axis, dtype=X.dtype, device=X.device)
+        w = X - torch.as_tensor(self.centre, dtype=X.dtype, device=X.device)
+        h = (w * A).sum(-1, keepdim=True)
+        radial = w - h * A
+        r = radial.norm(dim=-1, keepdim=True)
+        cap = (h.abs() - self.half_len).abs() < (r - self.radius).abs()
+        side = radial / r.clamp(min=1e-300)
+        return torch.where(cap, torch.sign(h) * A, side)
+
 
 @dataclass
 class Box:
@@ -199,6 +221,16 @@ class Box:
         ok = (tnear <= tfar) & (tfar > 0)
         t = torch.where(tnear > 0, tnear, tfar)
         return torch.where(ok, t, torch.full_like(t, math.inf))
+
+    def normal_at(self, X):
+        # The face whose slab the point is closest to leaving: largest |p_k| / e_k
+        # in the box frame.
+        R = torch.as_tensor(self.rot, dtype=X.dtype, device=X.device)
+        p = (X - torch.as_tensor(self.centre, dtype=X.dtype, device=X.device)) @ R
+        e = torch.as_tensor(self.half, dtype=X.dtype, device=X.device)
+        k = (p.abs() / e).argmax(dim=-1, keepdim=True)
+        sgn = torch.sign(torch.gather(p, -1, k))
+        return sgn * R.T[k.squeeze(-1)]
 
 
 @dataclass
@@ -243,6 +275,40 @@ def cast(scene: Scene, W: int, H: int, K, device="cpu") -> torch.Tensor:
         sub = depth[r0:r1, c0:c1]
         torch.minimum(sub, t, out=sub)
     return depth
+
+
+def cast_normals(scene: Scene, W: int, H: int, K, device="cpu"):
+    """Nearest-hit z-depth (float64, H x W; +inf on a miss) and the exact
+    surface normal of the primitive hit there (float64, H x W x 3, unit),
+    oriented away from the camera (n . ray > 0, the convention of the
+    estimated normals); zero on a miss. Scene geometry only: the analytic
+    ground truth against which estimates are scored."""
+    fx, fy, cx, cy = K
+    dev = torch.device(device)
+    u_all = (torch.arange(W, dtype=torch.float64, device=dev) - cx) / fx
+    v_all = (torch.arange(H, dtype=torch.float64, device=dev) - cy) / fy
+    depth = torch.full((H, W), math.inf, dtype=torch.float64, device=dev)
+    normals = torch.zeros((H, W, 3), dtype=torch.float64, device=dev)
+    for p in scene.prims:
+        c0, c1, r0, r1 = _screen_rect(p.bound, K, W, H)
+        if c1 <= c0 or r1 <= r0:
+            continue
+        u = u_all[c0:c1].unsqueeze(0).expand(r1 - r0, c1 - c0)
+        v = v_all[r0:r1].unsqueeze(1).expand(r1 - r0, c1 - c0)
+        t = p.hit(u, v)
+        sub = depth[r0:r1, c0:c1]
+        closer = t < sub
+        if not bool(closer.any()):
+            continue
+        tt = torch.where(closer, t, torch.zeros_like(t))
+        X = torch.stack([tt * u, tt * v, tt], -1)
+        n = p.normal_at(X)
+        ray = torch.stack([u, v, torch.ones_like(u)], -1)
+        n = torch.where(((n * ray).sum(-1, keepdim=True) < 0), -n, n)
+        nsub = normals[r0:r1, c0:c1]
+        nsub[closer] = n[closer]
+        sub[closer] = t[closer]
+    return depth, normals
 
 
 # ------------------------------------------------------------------ scenes
@@ -309,6 +375,12 @@ def add_kinect_noise(depth: torch.Tensor, seed: int) -> torch.Tensor:
     z = torch.where(torch.isfinite(depth), depth, torch.zeros_like(depth))
     eps = torch.randn(depth.shape, generator=g, dtype=torch.float64, device=depth.device)
     return torch.where(torch.isfinite(depth), depth + KINECT_NOISE * z * z * eps, depth)
+
+
+def cfg1_normals(device="cpu") -> torch.Tensor:
+    """Exact surface normals of the 640x480 scene (H x W x 3 float64, oriented
+    away from the camera; zero where no surface is hit)."""
+    return cast_normals(cfg1_scene(), 640, 480, CFG1_K, device)[1]
 
 
 def cfg1_depth(device="cpu", noise=True, seed=1) -> tuple[torch.Tensor, tuple]:
