@@ -382,6 +382,24 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
         out[f"multiscale_{form}_1to4_hbm_frac"] = round(px * 19 / (ms / 1e3) / 1e9 / measured_peaks()[0], 4)
     pf.sync_status()
     del pf
+    # The same scales in one batched persistent launch per step.
+    mb = nrm.BatchedEstimator(nrm.NormalParams(), device=dev)
+    mfr, _ = mb.make_frames([(depth[i], Ks[i]) for i in range(N_FRAMES)],
+                            [(normals[i], valid[i]) for i in range(N_FRAMES)])
+    for form in ("pair", "quad"):
+        for _ in range(3):
+            mb.run_multiscale(mfr, N_FRAMES, (1, 2, 3, 4), form, stream)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(reps):
+            mb.run_multiscale(mfr, N_FRAMES, (1, 2, 3, 4), form, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        out[f"multiscale_{form}_1to4_batched_mpx_s"] = round(px / (ms / 1e3) / 1e6, 1)
+        out[f"multiscale_{form}_1to4_batched_hbm_frac"] = round(px * 19 / (ms / 1e3) / 1e9 / measured_peaks()[0], 4)
+    mb.sync_status()
+    del mb
 
     # Half output on the same batch (11 B/px).
     h16 = nrm.BatchedEstimator(nrm.NormalParams(out_dtype="f16"), device=dev)

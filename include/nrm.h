@@ -226,6 +226,15 @@ typedef struct {
 NRM_API int nrm_estimate_multiscale(nrm_handle* h, const void* depth, void* normals, uint8_t* valid,
                                     const nrm_scales* scales, void* cuda_stream);
 
+/* nrm_estimate_multiscale for n frames of any sizes, dtypes and intrinsics in
+ * one persistent launch (the batched pipeline of nrm_estimate_batched, tile
+ * 128 x 16, 256 compute threads). Frames as for nrm_estimate_batched; their
+ * points must be NULL (NRM_ERR_UNSUPPORTED otherwise). The per-scale constants
+ * are formed on the GPU from each frame's intrinsics, so results can differ
+ * from nrm_estimate_multiscale's in the last bits. n = 0 is a no-op. */
+NRM_API int nrm_estimate_batched_multiscale(nrm_handle* h, const nrm_frame* frames, int n, const nrm_scales* scales,
+                                            void* cuda_stream);
+
 /* Plane-fitting ("plane-PCA") normals, the ground truth the paper evaluates
  * against on real data (Section 1 describes the fit; Section 4 uses it with 25
  * neighbouring points, i.e. radius 2). For each pixel: the back-projected

@@ -225,17 +225,7 @@ class NormalEstimator(_Handle):
             raise ValueError(f"depth must be a contiguous ({self.H}, {self.W}) tensor")
         if _in_dtype(depth) != self.in_dtype:
             raise TypeError("depth dtype does not match the estimator's in_dtype")
-        alphas = [int(a) for a in alphas]
-        if not 1 <= len(alphas) <= _lib.NRM_MAX_SCALES:
-            raise ValueError(f"between 1 and {_lib.NRM_MAX_SCALES} scales")
-        forms = {"pair": _lib.NRM_MS_PAIR, "quad": _lib.NRM_MS_QUAD}
-        if form not in forms:
-            raise ValueError(f"form must be one of {tuple(forms)}")
-        sc = _lib.Scales()
-        sc.n_scales = len(alphas)
-        for i, a in enumerate(alphas):
-            sc.alpha[i] = a
-        sc.form = forms[form]
+        sc = _scales(alphas, form)
         if normals is None or valid is None:
             normals, valid = self.new_outputs()
         _lib.check(self.lib.nrm_estimate_multiscale(self.h, depth.data_ptr(), normals.data_ptr(), valid.data_ptr(),
@@ -263,6 +253,21 @@ class NormalEstimator(_Handle):
         _lib.check(self.lib.nrm_plane_fit(self.h, depth.data_ptr(), normals.data_ptr(), valid.data_ptr(),
                                           int(radius), _stream_ptr(stream)), "nrm_plane_fit")
         return normals, valid
+
+
+def _scales(alphas, form: str) -> _lib.Scales:
+    alphas = [int(a) for a in alphas]
+    if not 1 <= len(alphas) <= _lib.NRM_MAX_SCALES:
+        raise ValueError(f"between 1 and {_lib.NRM_MAX_SCALES} scales")
+    forms = {"pair": _lib.NRM_MS_PAIR, "quad": _lib.NRM_MS_QUAD}
+    if form not in forms:
+        raise ValueError(f"form must be one of {tuple(forms)}")
+    sc = _lib.Scales()
+    sc.n_scales = len(alphas)
+    for i, a in enumerate(alphas):
+        sc.alpha[i] = a
+    sc.form = forms[form]
+    return sc
 
 
 def _check_points(points: torch.Tensor, H: int, W: int, out_pitch: int):
@@ -342,6 +347,19 @@ class BatchedEstimator(_Handle):
     def __call__(self, items: Sequence, outputs: Sequence | None = None, stream=None, points: bool = False):
         arr, outs = self.make_frames(items, outputs, points)
         self.run(arr, len(items), stream)
+        return outs
+
+    def run_multiscale(self, frames_array, n: int, alphas=(1, 2, 3, 4), form: str = "pair", stream=None):
+        """Multi-scale variant (Section 2's scale average; see
+        ``NormalEstimator.estimate_multiscale``) of a batch in one launch."""
+        sc = _scales(alphas, form)
+        _lib.check(self.lib.nrm_estimate_batched_multiscale(self.h, frames_array, int(n), ctypes.byref(sc),
+                                                            _stream_ptr(stream)), "nrm_estimate_batched_multiscale")
+
+    def multiscale(self, items: Sequence, alphas=(1, 2, 3, 4), form: str = "pair", outputs: Sequence | None = None,
+                   stream=None):
+        arr, outs = self.make_frames(items, outputs)
+        self.run_multiscale(arr, len(items), alphas, form, stream)
         return outs
 
     def run_host(self, depth_host: torch.Tensor, Ks: Sequence, normals_host: torch.Tensor,

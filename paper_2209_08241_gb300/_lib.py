@@ -92,6 +92,8 @@ SIGNATURES = [
                                      ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, _S]),
     ("nrm_estimate_multiscale", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.POINTER(Scales), _S]),
+    ("nrm_estimate_batched_multiscale", ctypes.c_int, [_H, ctypes.POINTER(Frame), ctypes.c_int,
+                                                       ctypes.POINTER(Scales), _S]),
     ("nrm_plane_fit", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _S]),
     ("nrm_sync_status", ctypes.c_int, [_H]),
     ("nrm_get_config", ctypes.c_int, [_H, ctypes.POINTER(TileConfig)]),

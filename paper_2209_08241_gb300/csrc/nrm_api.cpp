@@ -923,17 +923,13 @@ int nrm_angle_mse(nrm_handle* h, const float* normals, const uint8_t* valid, con
   return NRM_OK;
 }
 
-int nrm_estimate_multiscale(nrm_handle* h, const void* depth, void* normals, uint8_t* valid,
-                            const nrm_scales* scales, void* cuda_stream) {
-  g_last_error.clear();
-  if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
-  if (h->H == 0 || h->W == 0) return fail(NRM_ERR_INVALID_ARG, "handle was created for batched calls only");
+// Checks a scale set and fills ms.K, ms.alpha and ms.alpha_max.
+static int make_scales(const nrm_scales* scales, nrm::MsConsts& ms) {
   if (!scales) return fail(NRM_ERR_INVALID_ARG, "scales is NULL");
   const int K = scales->n_scales;
   if (K < 1 || K > NRM_MAX_SCALES) return fail(NRM_ERR_UNSUPPORTED, "n_scales %d outside 1..%d", K, NRM_MAX_SCALES);
   if (scales->form != NRM_MS_PAIR && scales->form != NRM_MS_QUAD)
     return fail(NRM_ERR_INVALID_ARG, "form %d", scales->form);
-  nrm::MsConsts ms;
   std::memset(&ms, 0, sizeof(ms));
   ms.K = K;
   for (int i = 0; i < K; ++i) {
@@ -942,6 +938,87 @@ int nrm_estimate_multiscale(nrm_handle* h, const void* depth, void* normals, uin
     ms.alpha[i] = a;
     ms.alpha_max = std::max(ms.alpha_max, a);
   }
+  return NRM_OK;
+}
+
+int nrm_estimate_batched_multiscale(nrm_handle* h, const nrm_frame* frames, int n, const nrm_scales* scales,
+                                    void* cuda_stream) {
+  g_last_error.clear();
+  if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 0) return fail(NRM_ERR_INVALID_ARG, "n < 0");
+  nrm::MsConsts ms;
+  int rc = make_scales(scales, ms);
+  if (rc) return rc;
+  if (n == 0) return NRM_OK;
+  if (!frames) return fail(NRM_ERR_INVALID_ARG, "frames is NULL");
+  const int TX = nrm::kMsTileX, TY = nrm::kMsTileY;
+  long long total = 0;
+  bool u16 = true;
+  for (int i = 0; i < n; ++i) {
+    rc = validate_frame(frames[i], i, h->p.out_dtype);
+    if (rc) return rc;
+    if (frames[i].points) return fail(NRM_ERR_UNSUPPORTED, "frame %d: the multi-scale variant writes no point clouds", i);
+    total += (long long)((frames[i].W + TX - 1) / TX) * ((frames[i].H + TY - 1) / TY);
+    if (total >= (1LL << 31) - 1) return fail(NRM_ERR_UNSUPPORTED, "batch exceeds 2^31 tiles");
+    u16 = u16 && (frames[i].in_dtype == NRM_IN_U16_MM || (long long)frames[i].H * frames[i].W == 0);
+  }
+  if (total == 0) return NRM_OK;
+  DeviceGuard guard(h->device);
+  Slot& s = h->slots[h->next_slot];
+  h->next_slot = (h->next_slot + 1) % kSlots;
+  rc = retire_slot(h, s);
+  if (rc) return rc;
+  rc = ensure_slot_capacity(h, s, n);
+  if (rc) return rc;
+  char* base = static_cast<char*>(s.host);
+  nrm::BatchHeader* hdr = reinterpret_cast<nrm::BatchHeader*>(base);
+  int* tb = reinterpret_cast<int*>(base + nrm::kTileBeginOffset);
+  FrameDesc* fd = reinterpret_cast<FrameDesc*>(base + nrm::frames_offset(s.capacity));
+  const double q = scales->form == NRM_MS_QUAD ? 4.0 : 1.0;
+  int acc = 0;
+  for (int i = 0; i < n; ++i) {
+    const nrm_frame& f = frames[i];
+    const int eb = f.in_dtype == NRM_IN_U16_MM ? 2 : 4;
+    make_desc(&fd[i], f.depth, f.normals, f.valid, f.H, f.W, f.depth_pitch, f.out_pitch, f.K, f.in_dtype, h->p,
+              TX, TY, TX + 2 * nrm::pad_x(ms.alpha_max, eb), TY + 2 * ms.alpha_max);
+    // Per-frame bases; the kernel scales them by alpha_i (a, b) and alpha_i^2 (c).
+    const double sc = f.in_dtype == NRM_IN_U16_MM ? (double)h->p.depth_scale : 1.0;
+    fd[i].a = (float)(sc * sc / (q * f.K.fy * ms.K));
+    fd[i].b = (float)(sc * sc / (q * f.K.fx * ms.K));
+    fd[i].c = (float)(sc * sc / (q * f.K.fx * f.K.fy * ms.K));
+    fd[i].tile_begin = acc;
+    tb[i] = acc;
+    acc += fd[i].tiles_x * ((f.H + TY - 1) / TY);
+  }
+  tb[n] = acc;
+  hdr->n_frames = n;
+  hdr->total_tiles = acc;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const size_t used = nrm::frames_offset(s.capacity) + sizeof(FrameDesc) * (size_t)n;
+  NRM_CUDA(cudaMemcpyAsync(s.dev, s.host, used, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+  nrm::BatchArgs args;
+  args.hdr = reinterpret_cast<const nrm::BatchHeader*>(s.dev);
+  args.tile_begin = reinterpret_cast<const int*>(static_cast<char*>(s.dev) + nrm::kTileBeginOffset);
+  args.frames = reinterpret_cast<const FrameDesc*>(static_cast<char*>(s.dev) + nrm::frames_offset(s.capacity));
+  nrm::Globals g = make_globals(h);
+  NRM_CUDA(nrm::launch_multiscale_batched(args, ms, g, h->p.out_dtype, scales->form, acc, u16, st),
+           "launch fwd_ms_persistent_kernel");
+  NRM_CUDA(cudaEventRecord(s.done, st), "cudaEventRecord");
+  s.in_flight = true;
+  s.timed_launch = false;
+  s.tiles = acc;
+  return NRM_OK;
+}
+
+int nrm_estimate_multiscale(nrm_handle* h, const void* depth, void* normals, uint8_t* valid,
+                            const nrm_scales* scales, void* cuda_stream) {
+  g_last_error.clear();
+  if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
+  if (h->H == 0 || h->W == 0) return fail(NRM_ERR_INVALID_ARG, "handle was created for batched calls only");
+  nrm::MsConsts ms;
+  int rc0 = make_scales(scales, ms);
+  if (rc0) return rc0;
+  const int K = ms.K;
   nrm_frame f = {};
   f.depth = depth;
   f.normals = normals;
@@ -954,6 +1031,7 @@ int nrm_estimate_multiscale(nrm_handle* h, const void* depth, void* normals, uin
   f.in_dtype = h->p.in_dtype;
   int rc = validate_frame(f, 0, h->p.out_dtype);
   if (rc) return rc;
+  if ((long long)f.H * f.W == 0) return NRM_OK;
   if ((f.H + nrm::kMsTileY - 1) / nrm::kMsTileY > 65535)
     return fail(NRM_ERR_UNSUPPORTED, "too many tile rows for the multi-scale launch");
   // Per-scale constants in FP64, rounded once, with 1/K, the depth scale^2 and

@@ -64,10 +64,10 @@ __global__ void __launch_bounds__(NT)
   compute_tile_any<TX, TY, NT, OUT, POINTS>(F, fw, pad4, tf, gx0, gy0, g);
 }
 
-// Block = NT compute threads + one producer warp.
-template <int TX, int TY, int NT, int OUT, bool POINTS>
-__global__ void __launch_bounds__(NT + 32)
-    fwd_persistent_kernel(const BatchArgs args, const Globals g) {
+// The persistent pipeline: block = NT compute threads + one producer warp.
+// compute(F, fw, pad4, tf, gx0, gy0) evaluates one decoded tile.
+template <int TX, int TY, int NT, class Compute>
+__device__ __forceinline__ void persistent_pipeline(const BatchArgs& args, const Globals& g, const Compute& compute) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int S = args.stages;
   const unsigned SB = args.stage_bytes;
@@ -173,8 +173,17 @@ __global__ void __launch_bounds__(NT + 32)
     }
     // Stage s and its record have been consumed by every compute thread.
     if (threadIdx.x == 0) mbar_arrive(smem_u32(&empty[s]));
-    compute_tile_any<TX, TY, NT, OUT, POINTS>(F, fw, pad4, si.f, gx0, gy0, g);
+    compute(F, fw, pad4, si.f, gx0, gy0);
   }
+}
+
+template <int TX, int TY, int NT, int OUT, bool POINTS>
+__global__ void __launch_bounds__(NT + 32)
+    fwd_persistent_kernel(const BatchArgs args, const Globals g) {
+  persistent_pipeline<TX, TY, NT>(args, g,
+                                  [&](const float* F, int fw, int pad4, const TileFrame& tf, int gx0, int gy0) {
+                                    compute_tile_any<TX, TY, NT, OUT, POINTS>(F, fw, pad4, tf, gx0, gy0, g);
+                                  });
 }
 
 }  // namespace nrm

@@ -199,6 +199,14 @@ struct MsConsts {
 // (kMsTileY + 2 alpha_max) (or fd.use_tma = 0).
 cudaError_t launch_multiscale(const FrameDesc& fd, const MsConsts& ms, const Globals& g, int out_dtype, int form,
                               cudaStream_t stream);
+// The batched form: one persistent launch over the batch's work list in a
+// device descriptor block (args; stages and stage bytes are set here). Each
+// frame's a, b, c hold its bases s^2 / (q fy K), s^2 / (q fx K),
+// s^2 / (q fx fy K) (s the depth scale, q = 1 for NRM_MS_PAIR and 4 for
+// NRM_MS_QUAD); ms.A, ms.B, ms.C are not used. u16: every frame is uint16.
+constexpr int kMsStages = 3;
+cudaError_t launch_multiscale_batched(const BatchArgs& args, const MsConsts& ms, const Globals& g, int out_dtype,
+                                      int form, int total_tiles, bool u16, cudaStream_t stream);
 
 // Plane-fitting ground truth (nrm_planefit.cu): FP32 normals (w = 0) and the
 // validity mask of the (2 radius + 1)^2 window fit; fd.depth, fd.normals,

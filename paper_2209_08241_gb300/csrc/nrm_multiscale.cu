@@ -12,12 +12,17 @@
 // (compute_tile_with). Both stencils give n_z = -u1 n_x - v1 n_y + n . ray, so
 // only n_x, n_y and n . ray are accumulated.
 //
-// One CTA per 128 x 16 tile with a halo of the largest scale, staged by TMA
-// (or plain loads) and decoded once; the per-pixel work is K stencil
-// evaluations from shared memory, so the kernel stays HBM-bound for small K.
+// fwd_ms_kernel: one CTA per 128 x 16 tile of one frame, with a halo of the
+// largest scale, staged by TMA (or plain loads) and decoded once; the
+// per-pixel work is K stencil evaluations from shared memory.
+// fwd_ms_persistent_kernel: the batched form, on the persistent pipeline of
+// the single-scale batched kernel (producer warp, TMA stage ring); each
+// frame's descriptor carries its base constants a, b, c (see
+// launch_multiscale_batched), scaled per scale by alpha_i and alpha_i^2.
+#include <algorithm>
 #include <atomic>
 
-#include "nrm_device.cuh"
+#include "nrm_forward_kernels.cuh"
 
 namespace nrm {
 
@@ -101,6 +106,79 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
+// Per-frame form of MultiStencil: the constants of scale i are alpha_i a,
+// alpha_i b, alpha_i^2 c from the frame's (sign-folded) bases.
+template <int FORM>
+struct FrameMultiStencil {
+  const MsConsts* ms;
+  float a, b, c;
+  int bw;
+  __device__ __forceinline__ void operator()(const float* pa, const float* pb, float2 d1, float2& nx, float2& ny,
+                                             float2& P) const {
+    const float2 M1 = f2(-1.0f, -1.0f);
+    float2 ax = f2(-0.f, -0.f), ay = f2(-0.f, -0.f), ap = f2(-0.f, -0.f);
+#pragma unroll 1
+    for (int i = 0; i < ms->K; ++i) {
+      const int al = ms->alpha[i];
+      const int dv = al * bw;
+      const float fa = (float)al;
+      const float sa = fa * a, sb = fa * b, sc = fa * fa * c;
+      const float2 A = f2(sa, sa), B = f2(sb, sb), C = f2(sc, sc);
+      const float2 d2 = f2(pa[al], pb[al]);
+      const float2 d3 = f2(pa[dv], pb[dv]);
+      if (FORM == NRM_MS_PAIR) {
+        const float2 D21 = __ffma2_rn(M1, d1, d2), D31 = __ffma2_rn(M1, d1, d3);
+        ax = __ffma2_rn(__fmul2_rn(A, d3), D21, ax);
+        ay = __ffma2_rn(__fmul2_rn(B, d2), D31, ay);
+        ap = __ffma2_rn(__fmul2_rn(C, d2), d3, ap);
+      } else {
+        const float2 d4 = f2(pa[-al], pb[-al]);
+        const float2 d5 = f2(pa[-dv], pb[-dv]);
+        const float2 S24 = __fadd2_rn(d2, d4), D24 = __ffma2_rn(M1, d4, d2);
+        const float2 S35 = __fadd2_rn(d3, d5), D35 = __ffma2_rn(M1, d5, d3);
+        ax = __ffma2_rn(__fmul2_rn(A, S35), D24, ax);
+        ay = __ffma2_rn(__fmul2_rn(B, S24), D35, ay);
+        ap = __ffma2_rn(__fmul2_rn(C, S24), S35, ap);
+      }
+    }
+    nx = ax;
+    ny = ay;
+    P = ap;
+  }
+};
+
+template <int OUT, int FORM>
+__global__ void __launch_bounds__(NT + 32)
+    fwd_ms_persistent_kernel(const BatchArgs args, const __grid_constant__ MsConsts ms, const Globals g) {
+  persistent_pipeline<TX, TY, NT>(
+      args, g, [&](const float* F, int fw, int pad4, const TileFrame& tf, int gx0, int gy0) {
+        const FrameMultiStencil<FORM> st{&ms, tf.a, tf.b, tf.c, fw};
+        const bool full = gx0 + TX <= tf.W;
+        if (g.mask_mode == NRM_MASK_SECANT) {
+          if (full)
+            compute_tile_with<TX, TY, NT, OUT, true, true>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
+          else
+            compute_tile_with<TX, TY, NT, OUT, true, false>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
+        } else {
+          if (full)
+            compute_tile_with<TX, TY, NT, OUT, false, true>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
+          else
+            compute_tile_with<TX, TY, NT, OUT, false, false>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
+        }
+      });
+}
+
+const void* ms_persistent_kernel(int out_dtype, int form) {
+  static const void* k[3][2] = {
+      {(const void*)fwd_ms_persistent_kernel<NRM_OUT_F32X4, NRM_MS_PAIR>,
+       (const void*)fwd_ms_persistent_kernel<NRM_OUT_F32X4, NRM_MS_QUAD>},
+      {(const void*)fwd_ms_persistent_kernel<NRM_OUT_F16X4, NRM_MS_PAIR>,
+       (const void*)fwd_ms_persistent_kernel<NRM_OUT_F16X4, NRM_MS_QUAD>},
+      {(const void*)fwd_ms_persistent_kernel<NRM_OUT_OCT16, NRM_MS_PAIR>,
+       (const void*)fwd_ms_persistent_kernel<NRM_OUT_OCT16, NRM_MS_QUAD>}};
+  return k[out_dtype][form];
+}
+
 const void* ms_kernel(int out_dtype, int form) {
   static const void* k[3][2] = {
       {(const void*)fwd_ms_kernel<NRM_OUT_F32X4, NRM_MS_PAIR>, (const void*)fwd_ms_kernel<NRM_OUT_F32X4, NRM_MS_QUAD>},
@@ -134,6 +212,40 @@ cudaError_t launch_multiscale(const FrameDesc& fd, const MsConsts& ms, const Glo
   Globals gg = g;
   void* args[3] = {&d, &m, &gg};
   cudaError_t e = cudaLaunchKernel(fn, grid, dim3(NT), args, smem, stream);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_multiscale_batched(const BatchArgs& args, const MsConsts& ms, const Globals& g, int out_dtype,
+                                      int form, int total_tiles, bool u16, cudaStream_t stream) {
+  if (out_dtype < 0 || out_dtype > 2 || form < 0 || form > 1) return cudaErrorInvalidValue;
+  const void* fn = ms_persistent_kernel(out_dtype, form);
+  static std::atomic<bool> granted[3][2][64];
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 63;
+  if (!granted[out_dtype][form][dev].load()) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)persistent_smem_bytes(TX, TY, NRM_MAX_ALPHA, kMsStages));
+    if (e != cudaSuccess) return e;
+    granted[out_dtype][form][dev].store(true);
+  }
+  const unsigned smem = persistent_smem_bytes(TX, TY, ms.alpha_max, kMsStages, u16 ? 2 : 0);
+  int occ = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, persistent_threads(NT), smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  // Two CTAs of 256 compute threads per SM: 16 compute warps, the count at
+  // which the single-scale batched kernel writes to HBM fastest.
+  const int grid = std::min(total_tiles, std::min(occ, 2) * sms);
+  BatchArgs a = args;
+  a.stages = kMsStages;
+  a.stage_bytes = stage_bytes_for(TX, TY, ms.alpha_max, u16 ? 2 : 0);
+  MsConsts m = ms;
+  Globals gg = g;
+  gg.alpha = ms.alpha_max;
+  void* kargs[3] = {&a, &m, &gg};
+  e = cudaLaunchKernel(fn, dim3(grid), dim3(persistent_threads(NT)), kargs, smem, stream);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 

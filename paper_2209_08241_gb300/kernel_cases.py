@@ -10,6 +10,7 @@ Cases:
                  4096 x 3072 float32 frame
   multiscale     multi-scale variant, scales 1..4, stencil --form (pair or
                  quad), on a 4096 x 3072 float32 frame
+  multiscale_batch  the same, batched, on N full-HD uint16 frames (default 8)
 
 Each case runs the kernel ``--reps`` times after one untimed call and prints the
 mean time per call (CUDA events) and the algorithmic bandwidth.
@@ -98,9 +99,20 @@ def case_multiscale(form: str, reps: int):
     return ms, px, px * 21
 
 
+def case_multiscale_batch(form: str, frames: int, reps: int):
+    items = [scenes.random_frame(1000 + i, 1920, 1080, "cuda", kind="u16") for i in range(frames)]
+    b = nrm.BatchedEstimator()
+    outs = b.multiscale(items, (1, 2, 3, 4), form)
+    arr, _ = b.make_frames(items, outs)
+    ms = _time(lambda: b.run_multiscale(arr, frames, (1, 2, 3, 4), form), reps)
+    px = frames * 1920 * 1080
+    return ms, px, px * 19
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["forward", "adjoint", "adjoint_batch", "plane_fit", "multiscale"])
+    ap.add_argument("case", choices=["forward", "adjoint", "adjoint_batch", "plane_fit", "multiscale",
+                                     "multiscale_batch"])
     ap.add_argument("--radius", type=int, default=2)
     ap.add_argument("--form", choices=["pair", "quad"], default="pair")
     ap.add_argument("--reps", type=int, default=20)
@@ -114,6 +126,8 @@ def main(argv=None):
         ms, px, nbytes = case_plane_fit(a.radius, a.reps)
     elif a.case == "multiscale":
         ms, px, nbytes = case_multiscale(a.form, a.reps)
+    elif a.case == "multiscale_batch":
+        ms, px, nbytes = case_multiscale_batch(a.form, a.frames or 8, a.reps)
     else:
         ms, px, nbytes = case_adjoint_batch(a.frames or 32, a.reps)
     print(f"{a.case}: {ms:.4f} ms/call, {px / ms / 1e3:.1f} Mpx/s, {nbytes / ms / 1e6:.1f} GB/s algorithmic")

@@ -136,3 +136,42 @@ def test_bad_scales_are_rejected():
     assert rc == nrm._lib.NRM_ERR_INVALID_ARG
     assert est.lib.nrm_estimate_multiscale(est.h, d.data_ptr(), n.data_ptr(), m.data_ptr(), None, None) \
         == nrm._lib.NRM_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("form,alphas", [("pair", (1, 2, 3, 4)), ("quad", (1, 2, 3, 4)), ("pair", (1, 16)),
+                                         ("quad", (3,))])
+def test_batched_mixed_sizes_dtypes_and_intrinsics(form, alphas):
+    specs = [(1920, 1080, "u16"), (333, 197, "f32"), (640, 480, "u16"), (64, 64, "f32"), (17, 9, "f32")]
+    items = [scenes.random_frame(1600 + i, W, H, DEV, kind=k) for i, (W, H, k) in enumerate(specs)]
+    b = nrm.BatchedEstimator()
+    outs = b.multiscale(items, alphas, form)
+    b.sync_status()
+    p = nrm.NormalParams()
+    for (d, K), (n, m), (W, H, k) in zip(items, outs, specs):
+        D = d.cpu().numpy()
+        ref = multiscale(D, K, list(alphas), form, stat_mode(p), p.tau, p.depth_scale, 0)
+        kappa = ms_kappa(D, K, list(alphas), form, p.depth_scale)
+        compare_ms(n, m, ref, p.tau, kappa, what=f"batched {form} {alphas} {W}x{H} {k}")
+
+
+def test_batched_half_and_orientation():
+    items = [scenes.random_frame(1700 + i, 320, 240, DEV, kind="u16") for i in range(3)]
+    b = nrm.BatchedEstimator(nrm.NormalParams(out_dtype="f16", orient_to_camera=True))
+    outs = b.multiscale(items, (1, 2), "pair")
+    b.sync_status()
+    p = nrm.NormalParams()
+    for (d, K), (n, m) in zip(items, outs):
+        D = d.cpu().numpy()
+        ref = multiscale(D, K, [1, 2], "pair", stat_mode(p), p.tau, p.depth_scale, 1)
+        compare_ms(n, m, ref, p.tau, ms_kappa(D, K, [1, 2], "pair"), half=True, what="batched f16 orient")
+
+
+def test_batched_multiscale_rejects_point_buffers():
+    d, K = scenes.random_frame(1800, 64, 48, DEV, kind="f32")
+    b = nrm.BatchedEstimator()
+    n = torch.empty((48, 64, 4), device=DEV)
+    m = torch.empty((48, 64), dtype=torch.uint8, device=DEV)
+    P = torch.empty((48, 64, 4), device=DEV)
+    arr, _ = b.make_frames([(d, K)], [(n, m, P)])
+    with pytest.raises(nrm._lib.NrmError):
+        b.run_multiscale(arr, 1)
