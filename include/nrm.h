@@ -226,6 +226,21 @@ typedef struct {
 NRM_API int nrm_estimate_multiscale(nrm_handle* h, const void* depth, void* normals, uint8_t* valid,
                                     const nrm_scales* scales, void* cuda_stream);
 
+/* nrm_estimate_batched on frames whose depth, normals, valid and points are
+ * HOST pointers (page-locked memory for asynchronous copies; pageable memory
+ * works, with copies that return only once done). The library stages the
+ * frames in handle-owned device memory (allocated on first use and when a
+ * larger chunk is needed), splits the batch into chunks of consecutive frames
+ * (about 96 MB of staging each) on two internal streams, and for each chunk
+ * uploads the depth, runs the batched kernel and downloads normals, masks and
+ * points, so that uploads and kernels overlap earlier chunks' downloads. The
+ * work starts after everything already queued on cuda_stream, and cuda_stream
+ * waits for all of it: synchronise cuda_stream before reading the host
+ * outputs, and keep every buffer valid until then. Pitches are those of the
+ * host buffers. Results are those of nrm_estimate_batched, bit for bit. If an
+ * error is returned part of the batch may already be queued. */
+NRM_API int nrm_estimate_batched_host(nrm_handle* h, const nrm_frame* frames, int n, void* cuda_stream);
+
 /* nrm_estimate_multiscale for n frames of any sizes, dtypes and intrinsics in
  * one persistent launch (the batched pipeline of nrm_estimate_batched, tile
  * 128 x 16, 256 compute threads). Frames as for nrm_estimate_batched; their

@@ -362,33 +362,51 @@ class BatchedEstimator(_Handle):
         self.run_multiscale(arr, len(items), alphas, form, stream)
         return outs
 
-    def run_host(self, depth_host: torch.Tensor, Ks: Sequence, normals_host: torch.Tensor,
-                 valid_host: torch.Tensor, staging: dict | None = None, stream=None) -> dict:
-        """End-to-end call on HOST buffers for a stack of equal-size frames.
-
-        depth_host (n, H, W) float32/uint16, normals_host (n, H, W, 4) and
-        valid_host (n, H, W) uint8, all in pinned host memory. Copies the depth
-        to the device, runs one batched launch and copies normals and masks back,
-        all on one stream; returns the device staging buffers (reusable: pass
-        them back as ``staging``). The caller synchronises before reading."""
+    def make_host_frames(self, depth_host: torch.Tensor, Ks: Sequence, normals_host: torch.Tensor,
+                         valid_host: torch.Tensor, points_host: torch.Tensor | None = None):
+        """ctypes frame array with HOST pointers for ``run_host``: a stack of n
+        equal-size frames, depth (n, H, W) float32/uint16, normals
+        (n, H, W, C), valid (n, H, W) uint8 and optional points (n, H, W, 4)
+        float32, contiguous CPU tensors (page-locked for asynchronous copies)."""
         n, H, W = depth_host.shape
-        dev = self.device
-        if staging is None:
-            staging = {
-                "depth": torch.empty(depth_host.shape, dtype=depth_host.dtype, device=dev),
-                "normals": torch.empty(normals_host.shape, dtype=normals_host.dtype, device=dev),
-                "valid": torch.empty(valid_host.shape, dtype=torch.uint8, device=dev),
-            }
-            staging["frames"], _ = self.make_frames(
-                [(staging["depth"][i], Ks[i]) for i in range(n)],
-                [(staging["normals"][i], staging["valid"][i]) for i in range(n)])
-        s = stream if stream is not None else torch.cuda.current_stream(dev)
-        with torch.cuda.stream(s):
-            staging["depth"].copy_(depth_host, non_blocking=True)
-            self.run(staging["frames"], n, s)
-            normals_host.copy_(staging["normals"], non_blocking=True)
-            valid_host.copy_(staging["valid"], non_blocking=True)
-        return staging
+        C = self.params.out_channels
+        tensors = [depth_host, normals_host, valid_host] + ([points_host] if points_host is not None else [])
+        for t in tensors:
+            if t.device.type != "cpu" or not t.is_contiguous():
+                raise ValueError("host buffers must be contiguous CPU tensors")
+        if tuple(normals_host.shape) != (n, H, W, C) or normals_host.dtype != self.params.torch_out_dtype \
+                or tuple(valid_host.shape) != (n, H, W) or valid_host.dtype != torch.uint8:
+            raise ValueError(f"normals must be (n, H, W, {C}) {self.params.torch_out_dtype}, valid (n, H, W) uint8")
+        if points_host is not None and (tuple(points_host.shape) != (n, H, W, 4)
+                                        or points_host.dtype != torch.float32):
+            raise ValueError("points must be (n, H, W, 4) float32")
+        arr = (_lib.Frame * max(n, 1))()
+        for i in range(n):
+            f = arr[i]
+            f.depth = depth_host[i].data_ptr()
+            f.normals = normals_host[i].data_ptr()
+            f.valid = valid_host[i].data_ptr()
+            f.H, f.W = int(H), int(W)
+            f.depth_pitch = f.out_pitch = int(W)
+            f.K = _intr(Ks[i])
+            f.in_dtype = _in_dtype(depth_host)
+            if points_host is not None:
+                f.points = points_host[i].data_ptr()
+        return arr
+
+    def run_host(self, depth_host: torch.Tensor, Ks: Sequence, normals_host: torch.Tensor,
+                 valid_host: torch.Tensor, frames=None, stream=None, points_host: torch.Tensor | None = None):
+        """End-to-end call on HOST buffers (``nrm_estimate_batched_host``): the
+        library uploads, computes and downloads in overlapped chunks on its own
+        streams, after everything already queued on ``stream``, which waits for
+        it; synchronise ``stream`` before reading the outputs. Returns the frame
+        array (pass it back as ``frames`` to skip rebuilding it)."""
+        n = depth_host.shape[0]
+        if frames is None:
+            frames = self.make_host_frames(depth_host, Ks, normals_host, valid_host, points_host)
+        _lib.check(self.lib.nrm_estimate_batched_host(self.h, frames, int(n), _stream_ptr(stream)),
+                   "nrm_estimate_batched_host")
+        return frames
 
     def make_grad_frames(self, items: Sequence, grad_normals: Sequence, valids: Sequence,
                          grad_depths: Sequence | None = None):

@@ -92,6 +92,7 @@ SIGNATURES = [
                                      ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, _S]),
     ("nrm_estimate_multiscale", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.POINTER(Scales), _S]),
+    ("nrm_estimate_batched_host", ctypes.c_int, [_H, ctypes.POINTER(Frame), ctypes.c_int, _S]),
     ("nrm_estimate_batched_multiscale", ctypes.c_int, [_H, ctypes.POINTER(Frame), ctypes.c_int,
                                                        ctypes.POINTER(Scales), _S]),
     ("nrm_plane_fit", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _S]),

@@ -235,6 +235,15 @@ struct BSlot {
   bool in_flight = false;
 };
 
+// One internal stream of the host-buffer pipeline and its device staging.
+struct HostLane {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;  // after the lane's last operation of a call
+  void* dev = nullptr;         // staging of one chunk: depth, normals, mask, points
+  size_t bytes = 0;
+};
+constexpr int kLanes = 2;
+
 }  // namespace
 
 struct nrm_handle {
@@ -262,6 +271,8 @@ struct nrm_handle {
   nrm_stats stats = {0, 0.0, 0};
   cudaEvent_t last_single = nullptr;  // after the latest plain / backward launch
   double* d_mse_partials = nullptr;   // nrm_angle_mse scratch (3 kMseBlocks doubles)
+  HostLane lanes[kLanes];             // nrm_estimate_batched_host pipeline
+  cudaEvent_t host_start = nullptr;
   std::vector<FrameDesc> scratch_desc;
 };
 
@@ -665,6 +676,13 @@ void nrm_destroy(nrm_handle* h) {
     cudaEventSynchronize(h->last_single);
     cudaEventDestroy(h->last_single);
   }
+  for (auto& l : h->lanes) {
+    if (l.stream) cudaStreamSynchronize(l.stream);
+    if (l.dev) cudaFree(l.dev);
+    if (l.done) cudaEventDestroy(l.done);
+    if (l.stream) cudaStreamDestroy(l.stream);
+  }
+  if (h->host_start) cudaEventDestroy(h->host_start);
   if (h->d_status) cudaFree(h->d_status);
   if (h->d_mse_partials) cudaFree(h->d_mse_partials);
   delete h;
@@ -777,6 +795,145 @@ int nrm_estimate_batched(nrm_handle* h, const nrm_frame* frames, int n, void* cu
   s.in_flight = true;
   s.timed_launch = s.graph_timed;
   s.tiles = acc;
+  return NRM_OK;
+}
+
+// ---------------------------------------------------------- host buffers
+
+namespace {
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Bytes of one frame's dense device staging: depth, normals, mask, points.
+struct StageSizes {
+  size_t depth, normals, valid, points;
+  size_t total() const { return depth + normals + valid + points; }
+};
+
+StageSizes stage_sizes(const nrm_frame& f, int out_dtype) {
+  const size_t px = (size_t)f.H * (size_t)f.W;
+  const size_t eb = f.in_dtype == NRM_IN_U16_MM ? 2 : 4;
+  const size_t ob = out_dtype == NRM_OUT_F32X4 ? 16 : (out_dtype == NRM_OUT_F16X4 ? 8 : 4);
+  return {align256(px * eb), align256(px * ob), align256(px), f.points ? align256(px * 16) : 0};
+}
+
+// Row copy of a (H x row_bytes) block between pitched host memory and dense
+// device memory (one cudaMemcpyAsync when the host rows are contiguous).
+int copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, size_t row_bytes, int rows,
+              cudaMemcpyKind kind, cudaStream_t st) {
+  if (dpitch == row_bytes && spitch == row_bytes) {
+    NRM_CUDA(cudaMemcpyAsync(dst, src, row_bytes * (size_t)rows, kind, st), "cudaMemcpyAsync");
+  } else {
+    NRM_CUDA(cudaMemcpy2DAsync(dst, dpitch, src, spitch, row_bytes, rows, kind, st), "cudaMemcpy2DAsync");
+  }
+  return NRM_OK;
+}
+
+}  // namespace
+
+int nrm_estimate_batched_host(nrm_handle* h, const nrm_frame* frames, int n, void* cuda_stream) {
+  g_last_error.clear();
+  if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 0) return fail(NRM_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return NRM_OK;
+  if (!frames) return fail(NRM_ERR_INVALID_ARG, "frames is NULL");
+  const int out = h->p.out_dtype;
+  for (int i = 0; i < n; ++i) {
+    const nrm_frame& f = frames[i];
+    if (f.H < 0 || f.W < 0) return fail(NRM_ERR_INVALID_ARG, "frame %d: negative size", i);
+    if ((long long)f.H * f.W == 0) continue;
+    if (!f.depth || !f.normals || !f.valid) return fail(NRM_ERR_INVALID_ARG, "frame %d: NULL buffer", i);
+    if (f.depth_pitch < f.W || f.out_pitch < f.W) return fail(NRM_ERR_INVALID_ARG, "frame %d: pitch < W", i);
+    if (f.in_dtype != NRM_IN_F32_M && f.in_dtype != NRM_IN_U16_MM)
+      return fail(NRM_ERR_INVALID_ARG, "frame %d: in_dtype %d", i, f.in_dtype);
+    if (f.H > (1 << 24) || f.W > (1 << 24)) return fail(NRM_ERR_UNSUPPORTED, "frame %d: dimension above 2^24", i);
+    if (validate_intrinsics(f.K)) return fail(NRM_ERR_INVALID_ARG, "frame %d: bad intrinsics", i);
+  }
+  // Chunks of consecutive frames with at least kChunkBytes of staging (or one
+  // frame), alternating between the lanes: a chunk's upload and kernel overlap
+  // the downloads of the chunks before it.
+  constexpr size_t kChunkBytes = size_t(96) << 20;
+  std::vector<std::pair<int, int>> chunks;  // [first, last)
+  size_t max_chunk = 0;
+  for (int i = 0; i < n;) {
+    size_t bytes = 0;
+    int j = i;
+    while (j < n && (j == i || bytes < kChunkBytes)) {
+      bytes += stage_sizes(frames[j], out).total();
+      ++j;
+    }
+    chunks.emplace_back(i, j);
+    max_chunk = std::max(max_chunk, bytes);
+    i = j;
+  }
+  DeviceGuard guard(h->device);
+  if (!h->host_start) NRM_CUDA(cudaEventCreateWithFlags(&h->host_start, cudaEventDisableTiming), "cudaEventCreate");
+  for (auto& l : h->lanes) {
+    if (!l.stream) NRM_CUDA(cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!l.done) NRM_CUDA(cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming), "cudaEventCreate");
+    if (l.bytes < max_chunk) {
+      NRM_CUDA(cudaStreamSynchronize(l.stream), "cudaStreamSynchronize");
+      if (l.dev) cudaFree(l.dev);
+      l.dev = nullptr;
+      l.bytes = 0;
+      NRM_CUDA(cudaMalloc(&l.dev, max_chunk), "cudaMalloc");
+      l.bytes = max_chunk;
+    }
+  }
+  cudaStream_t caller = static_cast<cudaStream_t>(cuda_stream);
+  NRM_CUDA(cudaEventRecord(h->host_start, caller), "cudaEventRecord");
+  for (auto& l : h->lanes) NRM_CUDA(cudaStreamWaitEvent(l.stream, h->host_start, 0), "cudaStreamWaitEvent");
+  std::vector<nrm_frame> dev_frames;
+  std::vector<size_t> offs;
+  for (size_t c = 0; c < chunks.size(); ++c) {
+    HostLane& l = h->lanes[c % kLanes];
+    char* base = static_cast<char*>(l.dev);
+    const int i0 = chunks[c].first, i1 = chunks[c].second;
+    dev_frames.clear();
+    size_t off = 0;
+    for (int i = i0; i < i1; ++i) {
+      const nrm_frame& f = frames[i];
+      const StageSizes sz = stage_sizes(f, out);
+      nrm_frame d = f;
+      d.depth = base + off;
+      d.normals = base + off + sz.depth;
+      d.valid = reinterpret_cast<uint8_t*>(base + off + sz.depth + sz.normals);
+      d.points = f.points ? reinterpret_cast<float*>(base + off + sz.depth + sz.normals + sz.valid) : nullptr;
+      d.depth_pitch = f.W;
+      d.out_pitch = f.W;
+      if ((long long)f.H * f.W > 0) {
+        const size_t eb = f.in_dtype == NRM_IN_U16_MM ? 2 : 4;
+        int rc = copy_rows(const_cast<void*>(d.depth), (size_t)f.W * eb, f.depth, (size_t)f.depth_pitch * eb,
+                           (size_t)f.W * eb, f.H, cudaMemcpyHostToDevice, l.stream);
+        if (rc) return rc;
+      }
+      dev_frames.push_back(d);
+      off += sz.total();
+    }
+    int rc = nrm_estimate_batched(h, dev_frames.data(), (int)dev_frames.size(), l.stream);
+    if (rc) return rc;
+    for (int i = i0; i < i1; ++i) {
+      const nrm_frame& f = frames[i];
+      const nrm_frame& d = dev_frames[i - i0];
+      if ((long long)f.H * f.W == 0) continue;
+      const size_t ob = out == NRM_OUT_F32X4 ? 16 : (out == NRM_OUT_F16X4 ? 8 : 4);
+      rc = copy_rows(f.normals, (size_t)f.out_pitch * ob, d.normals, (size_t)f.W * ob, (size_t)f.W * ob, f.H,
+                     cudaMemcpyDeviceToHost, l.stream);
+      if (rc) return rc;
+      rc = copy_rows(f.valid, (size_t)f.out_pitch, d.valid, (size_t)f.W, (size_t)f.W, f.H, cudaMemcpyDeviceToHost,
+                     l.stream);
+      if (rc) return rc;
+      if (f.points) {
+        rc = copy_rows(f.points, (size_t)f.out_pitch * 16, d.points, (size_t)f.W * 16, (size_t)f.W * 16, f.H,
+                       cudaMemcpyDeviceToHost, l.stream);
+        if (rc) return rc;
+      }
+    }
+  }
+  for (auto& l : h->lanes) {
+    NRM_CUDA(cudaEventRecord(l.done, l.stream), "cudaEventRecord");
+    NRM_CUDA(cudaStreamWaitEvent(caller, l.done, 0), "cudaStreamWaitEvent");
+  }
   return NRM_OK;
 }
 

@@ -92,3 +92,34 @@ def test_points_argument_checks():
     f.points = P.data_ptr()
     arr = (nrm._lib.Frame * 1)(f)
     assert lib.nrm_estimate_batched_noalloc(arr, 1, None, None, None) == nrm._lib.NRM_ERR_UNSUPPORTED
+
+
+def test_host_buffer_entry_point_matches_device_batch():
+    """nrm_estimate_batched_host (host buffers, chunked on internal streams)
+    returns what the device batch returns, bit for bit, including points.
+    Nine 1280 x 720 frames make three chunks on the two internal streams."""
+    n, H, W = 9, 720, 1280
+    items = [scenes.random_frame(1900 + i, W, H, DEV, kind="u16") for i in range(n)]
+    depth = torch.stack([d for d, _ in items])
+    Ks = [K for _, K in items]
+    b = nrm.BatchedEstimator()
+    P = torch.empty((n, H, W, 4), device=DEV)
+    ref = b([(depth[i], Ks[i]) for i in range(n)],
+            [(torch.empty((H, W, 4), device=DEV), torch.empty((H, W), dtype=torch.uint8, device=DEV), P[i])
+             for i in range(n)])
+    hd = depth.cpu().pin_memory()
+    hn = torch.empty((n, H, W, 4), pin_memory=True)
+    hv = torch.empty((n, H, W), dtype=torch.uint8, pin_memory=True)
+    hp = torch.empty((n, H, W, 4), pin_memory=True)
+    s = torch.cuda.Stream()
+    frames = b.run_host(hd, Ks, hn, hv, stream=s, points_host=hp)
+    s.synchronize()
+    for i in range(n):
+        assert torch.equal(hn[i], ref[i][0].cpu())
+        assert torch.equal(hv[i], ref[i][1].cpu())
+        assert torch.equal(hp[i], ref[i][2].cpu())
+    # Reusing the frame array on the default stream gives the same again.
+    hn.zero_()
+    b.run_host(hd, Ks, hn, hv, frames=frames)
+    torch.cuda.synchronize()
+    assert torch.equal(hn[n - 1], ref[n - 1][0].cpu())
