@@ -31,8 +31,20 @@ template <int p, int q>
 __device__ __forceinline__ void jacobi_rotate(float (&a)[3][3], float (&v)[3][3]) {
   const float apq = a[p][q];
   if (fabsf(apq) < 1e-35f) return;
-  const float theta = (a[q][q] - a[p][p]) / (2.0f * apq);
-  const float t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
+  // t = tan of the rotation angle, the smaller root of t^2 + 2 theta t - 1 = 0.
+  // Approximate reciprocal and square root suffice: c and s are formed from t
+  // so that c^2 + s^2 = 1 to rounding whatever t's last bits, and an error of a
+  // few ulp in t only leaves an off-diagonal residue of a few ulp of |a_pq|,
+  // the size of the rounding already in S.
+  const float theta = __fdividef(a[q][q] - a[p][p], 2.0f * apq);
+  const float at = fabsf(theta);
+  float t;
+  if (at > 1e18f) {
+    t = __fdividef(0.5f, theta);  // theta^2 would overflow; t = 1 / (2 theta) to rounding
+  } else {
+    const float h = fmaf(theta, theta, 1.0f);
+    t = __fdividef(copysignf(1.0f, theta), fmaf(h, rsqrtf(h), at));
+  }
   const float c = rsqrtf(fmaf(t, t, 1.0f));
   const float s = t * c;
   a[p][p] -= t * apq;
