@@ -269,6 +269,17 @@ NRM_API int nrm_estimate_batched_multiscale(nrm_handle* h, const nrm_frame* fram
 NRM_API int nrm_plane_fit(nrm_handle* h, const void* depth, float* normals, uint8_t* valid, int radius,
                           void* cuda_stream);
 
+/* Self-test of the bounded waits (no counterpart in the paper; a deployment
+ * check of failure reporting). On the current device, launches one block
+ * whose threads wait on a shared-memory barrier that nothing completes, with
+ * the same bounded waits every kernel here uses (warp-level and per-thread),
+ * for timeout_ns of GPU global time each (1e3 .. 1e9 ns, else
+ * NRM_ERR_INVALID_ARG). Both must give up and report NRM_ERR_TIMEOUT through a
+ * device status word. Synchronous. Returns NRM_OK if both reported the
+ * timeout (*elapsed_ms, if not NULL, gets the kernel's duration), or
+ * NRM_ERR_CUDA. Leaves the context usable; allocates and frees 8 bytes. */
+NRM_API int nrm_selftest_wait_expiry(unsigned long long timeout_ns, float* elapsed_ms);
+
 /* Waits for the handle's work, returns the device status word (NRM_OK or the
  * first device-side error since the last call) and clears it. */
 NRM_API int nrm_sync_status(nrm_handle* h);

@@ -96,6 +96,7 @@ SIGNATURES = [
     ("nrm_estimate_batched_multiscale", ctypes.c_int, [_H, ctypes.POINTER(Frame), ctypes.c_int,
                                                        ctypes.POINTER(Scales), _S]),
     ("nrm_plane_fit", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _S]),
+    ("nrm_selftest_wait_expiry", ctypes.c_int, [ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_float)]),
     ("nrm_sync_status", ctypes.c_int, [_H]),
     ("nrm_get_config", ctypes.c_int, [_H, ctypes.POINTER(TileConfig)]),
     ("nrm_set_config", ctypes.c_int, [_H, ctypes.POINTER(TileConfig)]),

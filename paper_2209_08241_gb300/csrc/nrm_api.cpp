@@ -1258,6 +1258,33 @@ int nrm_plane_fit(nrm_handle* h, const void* depth, float* normals, uint8_t* val
   return NRM_OK;
 }
 
+int nrm_selftest_wait_expiry(unsigned long long timeout_ns, float* elapsed_ms) {
+  g_last_error.clear();
+  if (timeout_ns < 1000ull || timeout_ns > 1000000000ull)
+    return fail(NRM_ERR_INVALID_ARG, "timeout_ns outside 1e3 .. 1e9");
+  int* d = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int host[2] = {0, 0};
+  int rc = NRM_OK;
+  cudaError_t e = cudaMalloc(&d, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(d, 0, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
+  if (e == cudaSuccess) e = nrm::launch_wait_expiry(timeout_ns, d, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaMemcpy(host, d, 2 * sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && elapsed_ms) e = cudaEventElapsedTime(elapsed_ms, e0, e1);
+  if (e != cudaSuccess) rc = fail(NRM_ERR_CUDA, "self-test: %s", cudaGetErrorString(e));
+  else if (host[0] != NRM_ERR_TIMEOUT || host[1] != NRM_ERR_TIMEOUT)
+    rc = fail(NRM_ERR_CUDA, "self-test: waits reported %d and %d instead of NRM_ERR_TIMEOUT", host[0], host[1]);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (d) cudaFree(d);
+  return rc;
+}
+
 int nrm_sync_status(nrm_handle* h) {
   if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
   DeviceGuard guard(h->device);

@@ -208,6 +208,10 @@ constexpr int kMsStages = 3;
 cudaError_t launch_multiscale_batched(const BatchArgs& args, const MsConsts& ms, const Globals& g, int out_dtype,
                                       int form, int total_tiles, bool u16, cudaStream_t stream);
 
+// Bounded-wait self-test (nrm_selftest.cu): status2 = two device ints (zeroed
+// by the caller), one per wait flavour.
+cudaError_t launch_wait_expiry(unsigned long long timeout_ns, int* status2, cudaStream_t stream);
+
 // Plane-fitting ground truth (nrm_planefit.cu): FP32 normals (w = 0) and the
 // validity mask of the (2 radius + 1)^2 window fit; fd.depth, fd.normals,
 // fd.valid, pitches, H, W, cx, cy, inv_fx, inv_fy and in_dtype are used;
