@@ -153,26 +153,10 @@ __device__ __forceinline__ void record_error(int* status, int code) {
 
 // -------------------------------------------------- per-pixel (adjoint path)
 
-// Depth validity and stencil sums for the adjoint kernel (float32 metres,
-// valid iff positive and finite).
+// Stencil sums and differences of Eq. 4-6 (adjoint kernel).
 struct StencilSums {
   float S24, D24, S35, D35;
-  bool ok;
 };
-
-__device__ __forceinline__ bool depth_ok(float d) { return d > 0.0f && d <= 3.402823466e38f; }
-
-__device__ __forceinline__ StencilSums stencil_sums(const float* p, int alpha, int bw) {
-  const float d1 = p[0], d2 = p[alpha], d4 = p[-alpha];
-  const float d3 = p[alpha * bw], d5 = p[-alpha * bw];
-  StencilSums s;
-  s.ok = depth_ok(d1) & depth_ok(d2) & depth_ok(d3) & depth_ok(d4) & depth_ok(d5);
-  s.S24 = d2 + d4;
-  s.D24 = d2 - d4;
-  s.S35 = d3 + d5;
-  s.D35 = d3 - d5;
-  return s;
-}
 
 struct FrameConsts {
   float a, b, c, inv_fx, inv_fy, cx, cy;
