@@ -16,10 +16,17 @@ pytestmark = pytest.mark.gpu
 NT = max(1, min(16, os.cpu_count() or 1))
 
 
-def test_u16_full_hd_batch_of_64():
+@pytest.mark.parametrize("config", ["default", "autotuned", (128, 16, 128, 2, 3)])
+def test_u16_full_hd_batch_of_64(config):
+    """The default launch geometry, the one the autotuner picks for this batch
+    (as bench.py does before timing), and the geometry it has been picking."""
     frames = scenes.u16_batch(64, 1920, 1080, device="cuda")
     p = nrm.NormalParams()
     b = nrm.BatchedEstimator(p)
+    if config == "autotuned":
+        b.autotune(frames)
+    elif config != "default":
+        b.set_config(*config)
     outs = b(frames)
     outs = b(frames, outputs=outs)  # second replay of the same graph slot ring
     b.sync_status()
@@ -29,4 +36,4 @@ def test_u16_full_hd_batch_of_64():
                              depth_scale=p.depth_scale, nthreads=NT)
         near, _, _ = compare(n, m, ref, p.tau, what=f"frame {i}")
         near_total += near
-    print(f"64 x 1080p u16: near-tau pixels excluded {near_total}")
+    print(f"64 x 1080p u16 {config} {b.config()}: near-tau pixels excluded {near_total}")
