@@ -150,7 +150,14 @@ NRM_API int nrm_estimate_points(nrm_handle* h, const void* depth, void* normals,
  * handle's alpha, mask mode, tau, depth_scale, out_dtype and orientation apply
  * to all frames. n = 0 is a no-op. The frames' buffers must not overlap. The
  * host may return before the GPU has read the descriptors; the handle keeps a
- * ring of descriptor slots and blocks only when every slot is still in use. */
+ * ring of descriptor slots and blocks only when every slot is still in use.
+ * Stream capture: while cuda_stream is being captured (any capture mode), the
+ * call records a single kernel node whose parameter holds all the frame
+ * descriptors and tensor maps (no device descriptor memory, copy or host
+ * synchronisation), so the captured graph can be replayed freely while the
+ * frames' buffers stay valid; then n is at most 100 and frames may not carry
+ * point buffers (NRM_ERR_UNSUPPORTED). The handle must have been configured
+ * (created or set_config / autotune) before the capture begins. */
 NRM_API int nrm_estimate_batched(nrm_handle* h, const nrm_frame* frames, int n, void* cuda_stream);
 
 /* Adjoint of nrm_estimate for float32 depth (derivatives of Eq. 4-6 and of the

@@ -23,7 +23,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnrm.so")
 
-SOURCES = ["nrm_forward.cu", "nrm_forward_points.cu", "nrm_backward.cu", "nrm_api.cpp", "nrm_noalloc.cu", "nrm_eval.cu", "nrm_planefit.cu", "nrm_multiscale.cu", "nrm_selftest.cu"]
+SOURCES = ["nrm_forward.cu", "nrm_forward_points.cu", "nrm_forward_param.cu", "nrm_backward.cu", "nrm_api.cpp", "nrm_noalloc.cu", "nrm_eval.cu", "nrm_planefit.cu", "nrm_multiscale.cu", "nrm_selftest.cu"]
 HEADERS = ["nrm_internal.h", "nrm_device.cuh", "nrm_forward_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

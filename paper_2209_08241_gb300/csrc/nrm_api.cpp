@@ -261,6 +261,8 @@ struct nrm_handle {
   const void* pts_plain = nullptr;       // the configuration's kernels that also write
   const void* pts_persistent = nullptr;  // point clouds (out dtype of p)
   int persistent_grid_pts[2] = {0, 0};
+  const void* param_persistent = nullptr;  // capture-safe kernel (descriptors as a parameter)
+  int persistent_grid_param[2] = {0, 0};
   int* d_status = nullptr;
   unsigned long long timeout_ns = kDefaultTimeoutNs;
   Slot slots[kSlots];
@@ -363,6 +365,8 @@ int configure(nrm_handle* h, const nrm_tile_config& c) {
   const unsigned ps = nrm::persistent_smem_bytes(c.tile_x, c.tile_y, h->p.alpha, c.stages);
   const unsigned pl = nrm::plain_smem_bytes(c.tile_x, c.tile_y, h->p.alpha);
   const void* pts_pers = nrm::fwd_points_kernel(c.tile_x, c.tile_y, c.threads, out, true);
+  const void* param_pers = nrm::fwd_param_kernel(c.tile_x, c.tile_y, c.threads, out);
+  if (!param_pers) return fail(NRM_ERR_UNSUPPORTED, "no capture-safe kernel for this configuration");
   const void* pts_plain = nrm::fwd_points_kernel(c.tile_x, c.tile_y, c.threads, out, false);
   if (!pts_pers || !pts_plain) return fail(NRM_ERR_UNSUPPORTED, "no point-cloud kernel for this configuration");
   int rc = set_smem_attr(ks->persistent[out], ps);
@@ -373,10 +377,12 @@ int configure(nrm_handle* h, const nrm_tile_config& c) {
   if (rc) return rc;
   rc = set_smem_attr(pts_plain, pl);
   if (rc) return rc;
+  rc = set_smem_attr(param_pers, ps);
+  if (rc) return rc;
   // CTAs per SM for each kernel and staging size (any dtype / uint16 only).
-  int per_sm[2][2];  // [points][u16]
-  const void* pk[2] = {ks->persistent[out], pts_pers};
-  for (int k = 0; k < 2; ++k)
+  int per_sm[3][2];  // [normal / points / parameter kernel][u16]
+  const void* pk[3] = {ks->persistent[out], pts_pers, param_pers};
+  for (int k = 0; k < 3; ++k)
     for (int u = 0; u < 2; ++u) {
       const unsigned bytes = nrm::persistent_smem_bytes(c.tile_x, c.tile_y, h->p.alpha, c.stages, u ? 2 : 0);
       int occ = 0;
@@ -394,7 +400,9 @@ int configure(nrm_handle* h, const nrm_tile_config& c) {
   for (int u = 0; u < 2; ++u) {
     h->persistent_grid[u] = per_sm[0][u] * h->sm_count;
     h->persistent_grid_pts[u] = per_sm[1][u] * h->sm_count;
+    h->persistent_grid_param[u] = per_sm[2][u] * h->sm_count;
   }
+  h->param_persistent = param_pers;
   h->pts_plain = pts_plain;
   h->pts_persistent = pts_pers;
   return NRM_OK;
@@ -737,6 +745,52 @@ int nrm_estimate_points(nrm_handle* h, const void* depth, void* normals, uint8_t
   return estimate_single(h, depth, normals, valid, points, cuda_stream);
 }
 
+// nrm_estimate_batched while cuda_stream is being captured: the descriptor
+// block travels as one kernel parameter, so the capture records a single
+// kernel node (no descriptor memory, upload, ring slot or synchronisation).
+// Frames were validated by the caller.
+static int estimate_batched_captured(nrm_handle* h, const nrm_frame* frames, int n, cudaStream_t st) {
+  if (n > nrm::kParamMaxFrames)
+    return fail(NRM_ERR_UNSUPPORTED, "at most %d frames per call during stream capture", nrm::kParamMaxFrames);
+  const int TX = h->cfg.tile_x, TY = h->cfg.tile_y;
+  std::vector<FrameDesc> fd((size_t)n);
+  std::vector<int> tb((size_t)n + 1);
+  bool u16 = true;
+  int acc = 0;
+  for (int i = 0; i < n; ++i) {
+    const nrm_frame& f = frames[i];
+    if (f.points && (long long)f.H * f.W > 0)
+      return fail(NRM_ERR_UNSUPPORTED, "frame %d: point clouds are not written during stream capture", i);
+    u16 = u16 && (f.in_dtype == NRM_IN_U16_MM || (long long)f.H * f.W == 0);
+    const int eb = f.in_dtype == NRM_IN_U16_MM ? 2 : 4;
+    make_desc(&fd[i], f.depth, f.normals, f.valid, f.H, f.W, f.depth_pitch, f.out_pitch, f.K, f.in_dtype, h->p,
+              TX, TY, TX + 2 * nrm::pad_x(h->p.alpha, eb), TY + 2 * h->p.alpha);
+    fd[i].tile_begin = acc;
+    tb[i] = acc;
+    acc += fd[i].tiles_x * ((f.H + TY - 1) / TY);
+  }
+  tb[n] = acc;
+  nrm::BatchHeader hdr;
+  std::memset(&hdr, 0, sizeof(hdr));
+  hdr.n_frames = n;
+  hdr.total_tiles = acc;
+  // The parameter block, 128-byte aligned like the records in it.
+  std::vector<unsigned char> raw(nrm::param_batch_bytes() + 128);
+  void* pb = raw.data() + (128 - reinterpret_cast<uintptr_t>(raw.data()) % 128) % 128;
+  nrm::pack_param_batch(pb, hdr, tb.data(), fd.data(), n);
+  nrm::BatchArgs ring;
+  std::memset(&ring, 0, sizeof(ring));
+  ring.stages = h->cfg.stages;
+  ring.stage_bytes = nrm::stage_bytes_for(TX, TY, h->p.alpha, u16 ? 2 : 0);
+  nrm::Globals g = make_globals(h);
+  void* args[3] = {pb, &ring, &g};
+  const unsigned smem = nrm::persistent_smem_bytes(TX, TY, h->p.alpha, h->cfg.stages, u16 ? 2 : 0);
+  NRM_CUDA(cudaLaunchKernel(h->param_persistent, dim3(h->persistent_grid_param[u16]),
+                            dim3(nrm::persistent_threads(h->cfg.threads)), args, smem, st),
+           "launch fwd_persistent_param_kernel");
+  return NRM_OK;
+}
+
 int nrm_estimate_batched(nrm_handle* h, const nrm_frame* frames, int n, void* cuda_stream) {
   g_last_error.clear();
   if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
@@ -754,6 +808,10 @@ int nrm_estimate_batched(nrm_handle* h, const nrm_frame* frames, int n, void* cu
   }
   if (total == 0) return NRM_OK;
   DeviceGuard guard(h->device);
+  cudaStream_t st0 = static_cast<cudaStream_t>(cuda_stream);
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  NRM_CUDA(cudaStreamIsCapturing(st0, &capture), "cudaStreamIsCapturing");
+  if (capture == cudaStreamCaptureStatusActive) return estimate_batched_captured(h, frames, n, st0);
   Slot& s = h->slots[h->next_slot];
   h->next_slot = (h->next_slot + 1) % kSlots;
   int rc = retire_slot(h, s);

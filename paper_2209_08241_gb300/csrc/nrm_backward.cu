@@ -254,7 +254,7 @@ cudaError_t launch_backward(const FrameDesc& fd, const BwdMaps& maps, const Glob
   Globals gg = g;
   void* args[3] = {&d, &m, &gg};
   e = cudaLaunchKernel(fn, grid, dim3(NT), args, smem, stream);
-  return e != cudaSuccess ? e : cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_backward_batched(const BwdBatchArgs& args, int n_frames, int max_tiles, const Globals& g,
@@ -267,7 +267,7 @@ cudaError_t launch_backward_batched(const BwdBatchArgs& args, int n_frames, int 
   Globals gg = g;
   void* kargs[2] = {&a, &gg};
   e = cudaLaunchKernel(fn, dim3(max_tiles, n_frames), dim3(NT), kargs, smem, stream);
-  return e != cudaSuccess ? e : cudaGetLastError();
+  return e;
 }
 
 }  // namespace nrm

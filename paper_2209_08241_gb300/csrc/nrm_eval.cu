@@ -122,20 +122,21 @@ __global__ void __launch_bounds__(kThreads) mse_final_kernel(const double* __res
 cudaError_t launch_spherical(const float* normals, const uint8_t* valid, int H, int W, long long pitch, float* phi,
                              float* theta, cudaStream_t stream) {
   dim3 grid((W + kThreads - 1) / kThreads, H < 65535 ? H : 65535);
-  spherical_kernel<<<grid, kThreads, 0, stream>>>(reinterpret_cast<const float4*>(normals), valid, H, W, pitch,
-                                                   phi, theta);
-  return cudaGetLastError();
+  const float4* n4 = reinterpret_cast<const float4*>(normals);
+  void* args[7] = {&n4, &valid, &H, &W, &pitch, &phi, &theta};
+  return cudaLaunchKernel((const void*)spherical_kernel, grid, dim3(kThreads), args, 0, stream);
 }
 
 cudaError_t launch_angle_mse(const float* na, const uint8_t* va, const float* nb, const uint8_t* vb, int H, int W,
                              long long pitch, double* partials, double* out, cudaStream_t stream) {
-  mse_partial_kernel<<<kMseBlocks, kThreads, 0, stream>>>(reinterpret_cast<const float4*>(na), va,
-                                                          reinterpret_cast<const float4*>(nb), vb, H, W, pitch,
-                                                          partials);
-  cudaError_t e = cudaGetLastError();
+  const float4* a4 = reinterpret_cast<const float4*>(na);
+  const float4* b4 = reinterpret_cast<const float4*>(nb);
+  void* pargs[8] = {&a4, &va, &b4, &vb, &H, &W, &pitch, &partials};
+  cudaError_t e = cudaLaunchKernel((const void*)mse_partial_kernel, dim3(kMseBlocks), dim3(kThreads), pargs, 0, stream);
   if (e != cudaSuccess) return e;
-  mse_final_kernel<<<1, kThreads, 0, stream>>>(partials, kMseBlocks, out);
-  return cudaGetLastError();
+  int nblocks = kMseBlocks;
+  void* fargs[3] = {&partials, &nblocks, &out};
+  return cudaLaunchKernel((const void*)mse_final_kernel, dim3(1), dim3(kThreads), fargs, 0, stream);
 }
 
 }  // namespace nrm

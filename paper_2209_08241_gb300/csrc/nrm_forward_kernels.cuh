@@ -64,9 +64,20 @@ __global__ void __launch_bounds__(NT)
   compute_tile_any<TX, TY, NT, OUT, POINTS>(F, fw, pad4, tf, gx0, gy0, g);
 }
 
+// A work-list index: through the read-only data path from global memory, or a
+// plain load from kernel-parameter space (GLOBAL = false).
+template <bool GLOBAL>
+__device__ __forceinline__ int load_index(const int* p) {
+  if (GLOBAL) return __ldg(p);
+  return *p;
+}
+
 // The persistent pipeline: block = NT compute threads + one producer warp.
-// compute(F, fw, pad4, tf, gx0, gy0) evaluates one decoded tile.
-template <int TX, int TY, int NT, class Compute>
+// compute(F, fw, pad4, tf, gx0, gy0) evaluates one decoded tile. FENCE: the
+// frame records (and their tensor maps) are in global memory written by the
+// host, so each map is fenced before its first use; false for records in
+// kernel-parameter space.
+template <int TX, int TY, int NT, class Compute, bool FENCE = true>
 __device__ __forceinline__ void persistent_pipeline(const BatchArgs& args, const Globals& g, const Compute& compute) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int S = args.stages;
@@ -108,9 +119,9 @@ __device__ __forceinline__ void persistent_pipeline(const BatchArgs& args, const
         return;
       }
       const int t = (int)blockIdx.x + j * G;
-      while (cur + 1 < nf && __ldg(args.tile_begin + cur + 1) <= t) ++cur;
+      while (cur + 1 < nf && load_index<FENCE>(args.tile_begin + cur + 1) <= t) ++cur;
       const FrameDesc* fd = args.frames + cur;
-      const int local = t - __ldg(args.tile_begin + cur);
+      const int local = t - load_index<FENCE>(args.tile_begin + cur);
       const int tiles_x = fd->tiles_x;
       const int ty = local / tiles_x;
       const int tx = local - ty * tiles_x;
@@ -122,7 +133,7 @@ __device__ __forceinline__ void persistent_pipeline(const BatchArgs& args, const
       si.frame = cur;
       const uint32_t bar = smem_u32(&full[s]);
       if (si.tma) {
-        if (cur != fenced) {
+        if (FENCE && cur != fenced) {
           fence_tensormap_acquire(&fd->tmap);
           fenced = cur;
         }
@@ -175,6 +186,27 @@ __device__ __forceinline__ void persistent_pipeline(const BatchArgs& args, const
     if (threadIdx.x == 0) mbar_arrive(smem_u32(&empty[s]));
     compute(F, fw, pad4, si.f, gx0, gy0);
   }
+}
+
+// The whole descriptor block of a batch as one kernel parameter (capture-safe
+// launches: nothing to upload, tensor maps in parameter space).
+struct alignas(128) ParamBatch {
+  BatchHeader hdr;
+  int tile_begin[kParamMaxFrames + 1];
+  FrameDesc frames[kParamMaxFrames];
+};
+
+template <int TX, int TY, int NT, int OUT>
+__global__ void __launch_bounds__(NT + 32)
+    fwd_persistent_param_kernel(const __grid_constant__ ParamBatch pb, const BatchArgs ring, const Globals g) {
+  BatchArgs args = ring;
+  args.hdr = &pb.hdr;
+  args.tile_begin = pb.tile_begin;
+  args.frames = pb.frames;
+  auto compute = [&](const float* F, int fw, int pad4, const TileFrame& tf, int gx0, int gy0) {
+    compute_tile_any<TX, TY, NT, OUT, false>(F, fw, pad4, tf, gx0, gy0, g);
+  };
+  persistent_pipeline<TX, TY, NT, decltype(compute), false>(args, g, compute);
 }
 
 template <int TX, int TY, int NT, int OUT, bool POINTS>

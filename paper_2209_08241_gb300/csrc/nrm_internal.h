@@ -73,6 +73,10 @@ struct Globals {
   unsigned long long timeout_ns;  // bound of every device-side wait
 };
 
+// Frames per capture-safe batched launch, whose descriptor block travels as
+// one kernel parameter (under the 32,764-byte parameter limit).
+constexpr int kParamMaxFrames = 100;
+
 struct BatchArgs {
   const BatchHeader* hdr;
   const int* tile_begin;
@@ -95,6 +99,12 @@ const FwdKernelSet* fwd_kernel_find(int tile_x, int tile_y, int threads);
 // The same configuration's kernel that also writes the point cloud
 // (nrm_forward_points.cu), or NULL.
 const void* fwd_points_kernel(int tile_x, int tile_y, int threads, int out_dtype, bool persistent);
+// The same configuration's persistent kernel taking the descriptor block as a
+// kernel parameter (nrm_forward_param.cu; capture-safe launches), its size in
+// bytes, and a host routine that packs a batch into that parameter block.
+const void* fwd_param_kernel(int tile_x, int tile_y, int threads, int out_dtype);
+size_t param_batch_bytes();
+void pack_param_batch(void* dst, const BatchHeader& hdr, const int* tile_begin, const FrameDesc* frames, int n);
 
 // Stage buffer bytes for a tile config and alpha: for input elements of eb
 // bytes (2: uint16, 4: float32), or the maximum over both (eb = 0).

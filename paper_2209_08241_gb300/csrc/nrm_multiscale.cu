@@ -212,7 +212,7 @@ cudaError_t launch_multiscale(const FrameDesc& fd, const MsConsts& ms, const Glo
   Globals gg = g;
   void* args[3] = {&d, &m, &gg};
   cudaError_t e = cudaLaunchKernel(fn, grid, dim3(NT), args, smem, stream);
-  return e != cudaSuccess ? e : cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_multiscale_batched(const BatchArgs& args, const MsConsts& ms, const Globals& g, int out_dtype,
@@ -246,7 +246,7 @@ cudaError_t launch_multiscale_batched(const BatchArgs& args, const MsConsts& ms,
   gg.alpha = ms.alpha_max;
   void* kargs[3] = {&a, &m, &gg};
   e = cudaLaunchKernel(fn, dim3(grid), dim3(persistent_threads(NT)), kargs, smem, stream);
-  return e != cudaSuccess ? e : cudaGetLastError();
+  return e;
 }
 
 }  // namespace nrm

@@ -159,14 +159,18 @@ __global__ void __launch_bounds__(PT)
 
 cudaError_t launch_plane_fit(const FrameDesc& fd, int radius, float sign, cudaStream_t stream) {
   dim3 grid((fd.W + PX - 1) / PX, (fd.H + PY - 1) / PY);
+  const void* fn = nullptr;
   switch (radius) {
-    case 1: plane_fit_kernel<1><<<grid, PT, 0, stream>>>(fd, sign); break;
-    case 2: plane_fit_kernel<2><<<grid, PT, 0, stream>>>(fd, sign); break;
-    case 3: plane_fit_kernel<3><<<grid, PT, 0, stream>>>(fd, sign); break;
-    case 4: plane_fit_kernel<4><<<grid, PT, 0, stream>>>(fd, sign); break;
+    case 1: fn = (const void*)plane_fit_kernel<1>; break;
+    case 2: fn = (const void*)plane_fit_kernel<2>; break;
+    case 3: fn = (const void*)plane_fit_kernel<3>; break;
+    case 4: fn = (const void*)plane_fit_kernel<4>; break;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  FrameDesc d = fd;
+  float sg = sign;
+  void* args[2] = {&d, &sg};
+  return cudaLaunchKernel(fn, grid, dim3(PT), args, 0, stream);
 }
 
 }  // namespace nrm

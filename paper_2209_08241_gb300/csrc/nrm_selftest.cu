@@ -31,8 +31,8 @@ __global__ void __launch_bounds__(64) wait_expiry_kernel(unsigned long long time
 }  // namespace
 
 cudaError_t launch_wait_expiry(unsigned long long timeout_ns, int* status2, cudaStream_t stream) {
-  wait_expiry_kernel<<<1, 64, 0, stream>>>(timeout_ns, status2);
-  return cudaGetLastError();
+  void* args[2] = {&timeout_ns, &status2};
+  return cudaLaunchKernel((const void*)wait_expiry_kernel, dim3(1), dim3(64), args, 0, stream);
 }
 
 }  // namespace nrm
