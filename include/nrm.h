@@ -188,7 +188,10 @@ typedef struct {
 
 /* nrm_backward for n float32 frames of any sizes and intrinsics in one launch
  * over all their tiles (the handle's alpha and orientation apply). Same
- * per-pixel arithmetic as nrm_backward. n = 0 is a no-op. */
+ * per-pixel arithmetic as nrm_backward. n = 0 is a no-op. Up to 60 frames the
+ * frame records and tensor maps travel as one kernel parameter (nothing to
+ * upload; the call can be recorded by stream capture); larger batches use a
+ * ring of device descriptor blocks. */
 NRM_API int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, void* cuda_stream);
 
 /* Spherical angle images of a normal map (Section 4, the I_phi and I_theta

@@ -55,6 +55,13 @@ int cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
+// Returns a nonzero status from a library routine.
+#define NRM_CHECK(call)       \
+  do {                        \
+    int rc_ = (call);         \
+    if (rc_) return rc_;      \
+  } while (0)
+
 // ------------------------------------------------ driver entry point (TMA)
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -289,6 +296,16 @@ nrm::Globals make_globals(const nrm_handle* h) {
   g.status = h->d_status;
   g.timeout_ns = h->timeout_ns;
   return g;
+}
+
+// Records the handle's "latest single launch" event on st, which
+// nrm_sync_status waits for; skipped while st is being captured (a captured
+// record belongs to the graph, not to this stream's timeline).
+int mark_single(nrm_handle* h, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  NRM_CUDA(cudaStreamIsCapturing(st, &cs), "cudaStreamIsCapturing");
+  if (cs == cudaStreamCaptureStatusNone) NRM_CUDA(cudaEventRecord(h->last_single, st), "cudaEventRecord");
+  return NRM_OK;
 }
 
 struct DeviceGuard {
@@ -728,7 +745,7 @@ static int estimate_single(nrm_handle* h, const void* depth, void* normals, uint
   NRM_CUDA(cudaLaunchKernel(points ? h->pts_plain : h->ks->plain[h->p.out_dtype], grid, dim3(h->cfg.threads),
                             args, nrm::plain_smem_bytes(TX, TY, h->p.alpha), st),
            "launch fwd_plain_kernel");
-  NRM_CUDA(cudaEventRecord(h->last_single, st), "cudaEventRecord");
+  NRM_CHECK(mark_single(h, st));
   return NRM_OK;
 }
 
@@ -1014,7 +1031,7 @@ int nrm_backward(nrm_handle* h, const void* depth, const float* grad_normals, co
   nrm::Globals g = make_globals(h);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   NRM_CUDA(nrm::launch_backward(d, maps, g, st), "launch bwd_kernel");
-  NRM_CUDA(cudaEventRecord(h->last_single, st), "cudaEventRecord");
+  NRM_CHECK(mark_single(h, st));
   return NRM_OK;
 }
 
@@ -1044,6 +1061,24 @@ int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, voi
   }
   if (total == 0) return NRM_OK;
   DeviceGuard guard(h->device);
+  if (n <= nrm::kBwdParamMaxFrames) {
+    // Small batches: records and tensor maps as one kernel parameter (no
+    // upload, no ring slot, no tensor-map fences; also capture-safe).
+    std::vector<FrameDesc> fdv((size_t)n);
+    std::vector<nrm::BwdMaps> mapv((size_t)n);
+    int max_tiles = 0;
+    for (int i = 0; i < n; ++i) {
+      const nrm_grad_frame& f = frames[i];
+      make_bwd_desc(&fdv[i], &mapv[i], f.depth, f.grad_normals, f.valid, f.grad_depth, f.H, f.W, f.depth_pitch,
+                    f.out_pitch, f.K, h->p);
+      max_tiles = std::max(max_tiles, fdv[i].tiles_x * ((f.H + TY - 1) / TY));
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    NRM_CUDA(nrm::launch_backward_batched_param(fdv.data(), mapv.data(), n, max_tiles, make_globals(h), st),
+             "launch bwd_batched_param_kernel");
+    NRM_CHECK(mark_single(h, st));
+    return NRM_OK;
+  }
   BSlot& s = h->bslots[h->next_bslot];
   h->next_bslot = (h->next_bslot + 1) % kSlots;
   if (s.in_flight) {
@@ -1134,7 +1169,7 @@ int nrm_angle_mse(nrm_handle* h, const float* normals, const uint8_t* valid, con
   NRM_CUDA(nrm::launch_angle_mse(normals, valid, ref_normals, ref_valid, H, W, pitch, h->d_mse_partials, out,
                                  static_cast<cudaStream_t>(cuda_stream)),
            "launch mse kernels");
-  NRM_CUDA(cudaEventRecord(h->last_single, static_cast<cudaStream_t>(cuda_stream)), "cudaEventRecord");
+  NRM_CHECK(mark_single(h, static_cast<cudaStream_t>(cuda_stream)));
   return NRM_OK;
 }
 
@@ -1271,7 +1306,7 @@ int nrm_estimate_multiscale(nrm_handle* h, const void* depth, void* normals, uin
   nrm::Globals g = make_globals(h);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   NRM_CUDA(nrm::launch_multiscale(d, ms, g, h->p.out_dtype, scales->form, st), "launch fwd_ms_kernel");
-  NRM_CUDA(cudaEventRecord(h->last_single, st), "cudaEventRecord");
+  NRM_CHECK(mark_single(h, st));
   return NRM_OK;
 }
 
@@ -1312,7 +1347,7 @@ int nrm_plane_fit(nrm_handle* h, const void* depth, float* normals, uint8_t* val
   d.in_dtype = f.in_dtype;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   NRM_CUDA(nrm::launch_plane_fit(d, radius, h->p.orient_to_camera ? -1.0f : 1.0f, st), "launch plane_fit_kernel");
-  NRM_CUDA(cudaEventRecord(h->last_single, st), "cudaEventRecord");
+  NRM_CHECK(mark_single(h, st));
   return NRM_OK;
 }
 

@@ -25,9 +25,11 @@
 // bwd_batched_kernel covers a batch (grid = max tiles of a frame x frames).
 // Both are compiled for alpha = 1..4 as constants (shared-memory offsets and
 // loop steps become immediates) and once for any alpha.
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <utility>
+#include <vector>
 
 #include "nrm_device.cuh"
 
@@ -209,6 +211,40 @@ __global__ void __launch_bounds__(NT) bwd_batched_kernel(const BwdBatchArgs args
   bwd_tile<ALPHA>(fd, &fd.tmap, &args.maps[f].grad, &args.maps[f].mask, tx * TX, ty * TY, g, smem);
 }
 
+// A batch of at most kBwdParamMaxFrames frames with its records and tensor
+// maps in kernel-parameter space: no descriptor upload and no tensor-map fence
+// (each CTA of the global-memory form fences three maps for its one tile).
+struct alignas(128) BwdParamBatch {
+  FrameDesc frames[kBwdParamMaxFrames];
+  BwdMaps maps[kBwdParamMaxFrames];
+};
+static_assert(sizeof(BwdParamBatch) <= 32764, "the descriptor block must fit the kernel parameter limit");
+
+// Grid (max tiles of a frame, frames), as bwd_batched_kernel.
+template <int ALPHA>
+__global__ void __launch_bounds__(NT)
+    bwd_batched_param_kernel(const __grid_constant__ BwdParamBatch pb, const Globals g) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int f = (int)blockIdx.y;
+  const FrameDesc& fd = pb.frames[f];
+  const int tiles_x = fd.tiles_x;
+  const int local = (int)blockIdx.x;
+  if (tiles_x == 0 || local >= tiles_x * ((fd.H + TY - 1) / TY)) return;
+  const int ty = local / tiles_x;
+  const int tx = local - ty * tiles_x;
+  bwd_tile<ALPHA>(fd, &fd.tmap, &pb.maps[f].grad, &pb.maps[f].mask, tx * TX, ty * TY, g, smem);
+}
+
+const void* bwd_param_kernel_for(int alpha) {
+  switch (alpha) {
+    case 1: return (const void*)bwd_batched_param_kernel<1>;
+    case 2: return (const void*)bwd_batched_param_kernel<2>;
+    case 3: return (const void*)bwd_batched_param_kernel<3>;
+    case 4: return (const void*)bwd_batched_param_kernel<4>;
+    default: return (const void*)bwd_batched_param_kernel<0>;
+  }
+}
+
 // The kernel for alpha: compiled for alpha = 1..4 (constant offsets and loop
 // steps), generic above.
 const void* bwd_kernel_for(int alpha, bool batched) {
@@ -268,6 +304,24 @@ cudaError_t launch_backward_batched(const BwdBatchArgs& args, int n_frames, int 
   void* kargs[2] = {&a, &gg};
   e = cudaLaunchKernel(fn, dim3(max_tiles, n_frames), dim3(NT), kargs, smem, stream);
   return e;
+}
+
+cudaError_t launch_backward_batched_param(const FrameDesc* frames, const BwdMaps* maps, int n_frames, int max_tiles,
+                                          const Globals& g, cudaStream_t stream) {
+  if (n_frames < 1 || n_frames > kBwdParamMaxFrames) return cudaErrorInvalidValue;
+  const unsigned smem = bwd_smem_bytes(g.alpha);
+  const void* fn = bwd_param_kernel_for(g.alpha);
+  cudaError_t e = set_smem(fn, smem);
+  if (e != cudaSuccess) return e;
+  std::vector<unsigned char> raw(sizeof(BwdParamBatch) + 128);
+  void* aligned = raw.data() + (128 - reinterpret_cast<uintptr_t>(raw.data()) % 128) % 128;
+  BwdParamBatch* pb = static_cast<BwdParamBatch*>(aligned);
+  std::memset(pb, 0, sizeof(BwdParamBatch));
+  std::memcpy(pb->frames, frames, sizeof(FrameDesc) * (size_t)n_frames);
+  std::memcpy(pb->maps, maps, sizeof(BwdMaps) * (size_t)n_frames);
+  Globals gg = g;
+  void* kargs[2] = {pb, &gg};
+  return cudaLaunchKernel(fn, dim3(max_tiles, n_frames), dim3(NT), kargs, smem, stream);
 }
 
 }  // namespace nrm

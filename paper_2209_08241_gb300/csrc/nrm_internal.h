@@ -182,6 +182,11 @@ cudaError_t launch_backward(const FrameDesc& fd, const BwdMaps& maps, const Glob
 // block is in device memory.
 cudaError_t launch_backward_batched(const BwdBatchArgs& args, int n_frames, int max_tiles, const Globals& g,
                                     cudaStream_t stream);
+// The same for at most kBwdParamMaxFrames frames with the records and maps
+// (host arrays) passed as one kernel parameter: no upload, no fences.
+constexpr int kBwdParamMaxFrames = 60;
+cudaError_t launch_backward_batched_param(const FrameDesc* frames, const BwdMaps* maps, int n_frames, int max_tiles,
+                                          const Globals& g, cudaStream_t stream);
 
 // Evaluation kernels (nrm_eval.cu).
 constexpr int kMseBlocks = 1024;  // fixed, so that the reduction order never changes

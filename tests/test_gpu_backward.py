@@ -129,10 +129,13 @@ def test_batch_of_32_losses():
     est.sync_status()
 
 
-def test_batched_adjoint_equals_per_frame_adjoint():
+@pytest.mark.parametrize("repeat", [1, 14])
+def test_batched_adjoint_equals_per_frame_adjoint(repeat):
     """One nrm_backward_batched launch over frames of different sizes and
-    intrinsics (ragged tails included) gives the per-frame results bit for bit."""
-    sizes = [(640, 480), (333, 197), (64, 16), (1280, 720), (100, 300)]
+    intrinsics (ragged tails included) gives the per-frame results bit for bit:
+    5 frames (descriptors as a kernel parameter) and 70 frames (descriptor ring
+    in device memory)."""
+    sizes = [(640, 480), (333, 197), (64, 16), (1280, 720), (100, 300)] * repeat
     frames = [scenes.random_frame(4100 + i, W, H, DEV, kind="f32", holes=True, clip_range=False)
               for i, (W, H) in enumerate(sizes)]
     b = nrm.BatchedEstimator()

@@ -62,3 +62,27 @@ def test_capture_limits_are_reported():
         with torch.cuda.graph(g, stream=torch.cuda.Stream()):
             b.run(arr, len(items), torch.cuda.current_stream())
     torch.cuda.synchronize()
+
+
+def test_batched_adjoint_captures_and_replays():
+    W, H, n = 320, 240, 6
+    items = [scenes.random_frame(2500 + i, W, H, DEV, kind="f32", holes=False, clip_range=False) for i in range(n)]
+    b = nrm.BatchedEstimator()
+    outs = b(items)
+    gs = []
+    for nm, m in outs:
+        g = torch.zeros_like(nm)
+        g[..., 2] = m.float()
+        gs.append(g)
+    ref = [x.clone() for x in b.backward(items, gs, [m for _, m in outs])]
+    grads = [torch.full_like(d, 7.0) for d, _ in items]
+    arr, _ = b.make_grad_frames(items, gs, [m for _, m in outs], grads)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=torch.cuda.Stream()):
+        b.run_backward(arr, n, torch.cuda.current_stream())
+    g.replay()
+    torch.cuda.synchronize()
+    b.sync_status()
+    for x, r in zip(grads, ref):
+        assert torch.equal(x, r)
