@@ -145,19 +145,21 @@ NRM_API int nrm_estimate_points(nrm_handle* h, const void* depth, void* normals,
                                 void* cuda_stream);
 
 /* n frames of any sizes, intrinsics and input dtypes in ONE persistent launch
- * over a (frame, tile) work list, replayed from a CUDA graph that the handle
- * captured once (a descriptor upload node followed by the kernel node). The
- * handle's alpha, mask mode, tau, depth_scale, out_dtype and orientation apply
- * to all frames. n = 0 is a no-op. The frames' buffers must not overlap. The
- * host may return before the GPU has read the descriptors; the handle keeps a
- * ring of descriptor slots and blocks only when every slot is still in use.
+ * over a (frame, tile) work list. The handle's alpha, mask mode, tau,
+ * depth_scale, out_dtype and orientation apply to all frames. n = 0 is a
+ * no-op. The frames' buffers must not overlap.
+ * Up to 100 frames without point buffers: the frame records and their TMA
+ * tensor maps travel as one kernel parameter (no descriptor upload, no
+ * tensor-map fences). Larger batches, or batches with point buffers: a CUDA
+ * graph per descriptor slot (upload node, then the kernel node), replayed
+ * from a ring of slots. Either way the host may return before the GPU has
+ * started; it blocks only when every slot of the ring is still in use.
  * Stream capture: while cuda_stream is being captured (any capture mode), the
- * call records a single kernel node whose parameter holds all the frame
- * descriptors and tensor maps (no device descriptor memory, copy or host
- * synchronisation), so the captured graph can be replayed freely while the
- * frames' buffers stay valid; then n is at most 100 and frames may not carry
- * point buffers (NRM_ERR_UNSUPPORTED). The handle must have been configured
- * (created or set_config / autotune) before the capture begins. */
+ * call records a single kernel node with the parameter form and no events or
+ * host synchronisation, so the captured graph can be replayed freely while
+ * the frames' buffers stay valid; then n is at most 100 and frames may not
+ * carry point buffers (NRM_ERR_UNSUPPORTED). The handle must have been
+ * configured (created, or set_config / autotune) before the capture begins. */
 NRM_API int nrm_estimate_batched(nrm_handle* h, const nrm_frame* frames, int n, void* cuda_stream);
 
 /* Adjoint of nrm_estimate for float32 depth (derivatives of Eq. 4-6 and of the

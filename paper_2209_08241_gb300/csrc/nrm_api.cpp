@@ -762,11 +762,13 @@ int nrm_estimate_points(nrm_handle* h, const void* depth, void* normals, uint8_t
   return estimate_single(h, depth, normals, valid, points, cuda_stream);
 }
 
-// nrm_estimate_batched while cuda_stream is being captured: the descriptor
-// block travels as one kernel parameter, so the capture records a single
-// kernel node (no descriptor memory, upload, ring slot or synchronisation).
-// Frames were validated by the caller.
-static int estimate_batched_captured(nrm_handle* h, const nrm_frame* frames, int n, cudaStream_t st) {
+// nrm_estimate_batched with the descriptor block as one kernel parameter
+// (frame records and tensor maps in parameter space): no descriptor upload and
+// no tensor-map fences. Used for batches of at most kParamMaxFrames frames
+// without point buffers, and always while cuda_stream is being captured, when
+// the launch is recorded as a single kernel node with no ring slot, events or
+// synchronisation. Frames were validated by the caller.
+static int estimate_batched_param(nrm_handle* h, const nrm_frame* frames, int n, cudaStream_t st, bool capture) {
   if (n > nrm::kParamMaxFrames)
     return fail(NRM_ERR_UNSUPPORTED, "at most %d frames per call during stream capture", nrm::kParamMaxFrames);
   const int TX = h->cfg.tile_x, TY = h->cfg.tile_y;
@@ -802,9 +804,25 @@ static int estimate_batched_captured(nrm_handle* h, const nrm_frame* frames, int
   nrm::Globals g = make_globals(h);
   void* args[3] = {pb, &ring, &g};
   const unsigned smem = nrm::persistent_smem_bytes(TX, TY, h->p.alpha, h->cfg.stages, u16 ? 2 : 0);
+  Slot* s = nullptr;
+  if (!capture) {
+    // A ring slot supplies the completion (and, with timing on, the kernel
+    // time) events; its descriptor memory is not used.
+    s = &h->slots[h->next_slot];
+    h->next_slot = (h->next_slot + 1) % kSlots;
+    NRM_CHECK(retire_slot(h, *s));
+    if (h->timing) NRM_CUDA(cudaEventRecord(s->ev_start, st), "cudaEventRecord");
+  }
   NRM_CUDA(cudaLaunchKernel(h->param_persistent, dim3(h->persistent_grid_param[u16]),
                             dim3(nrm::persistent_threads(h->cfg.threads)), args, smem, st),
            "launch fwd_persistent_param_kernel");
+  if (s) {
+    if (h->timing) NRM_CUDA(cudaEventRecord(s->ev_end, st), "cudaEventRecord");
+    NRM_CUDA(cudaEventRecord(s->done, st), "cudaEventRecord");
+    s->in_flight = true;
+    s->timed_launch = h->timing;
+    s->tiles = acc;
+  }
   return NRM_OK;
 }
 
@@ -828,7 +846,10 @@ int nrm_estimate_batched(nrm_handle* h, const nrm_frame* frames, int n, void* cu
   cudaStream_t st0 = static_cast<cudaStream_t>(cuda_stream);
   cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
   NRM_CUDA(cudaStreamIsCapturing(st0, &capture), "cudaStreamIsCapturing");
-  if (capture == cudaStreamCaptureStatusActive) return estimate_batched_captured(h, frames, n, st0);
+  if (capture == cudaStreamCaptureStatusActive) return estimate_batched_param(h, frames, n, st0, true);
+  bool any_points = false;
+  for (int i = 0; i < n; ++i) any_points = any_points || (frames[i].points && (long long)frames[i].H * frames[i].W > 0);
+  if (n <= nrm::kParamMaxFrames && !any_points) return estimate_batched_param(h, frames, n, st0, false);
   Slot& s = h->slots[h->next_slot];
   h->next_slot = (h->next_slot + 1) % kSlots;
   int rc = retire_slot(h, s);
