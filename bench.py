@@ -170,13 +170,32 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
-def time_oracle_on(frames_np, K, cores, budget_s=12.0):
-    """Runs the FP64 oracle over whole frames (each with all cores), cycling
-    through the given frames, until the budget is spent (at least one frame,
-    at most 64). Returns (Mpx/s, frames, seconds)."""
+def cpu_model() -> str:
+    """The host CPU's model string (x86 "model name", or Arm implementer/part)."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    if "model name" in fields:
+        return fields["model name"]
+    if "CPU part" in fields:
+        return f"{platform.machine()} implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+    return platform.machine()
+
+
+def time_oracle_on(frames_np, K, cores, budget_s=12.0, max_frames=4096):
+    """Runs the FP64 oracle over whole frames (each with `cores` threads),
+    cycling through the given frames, until the budget is spent (at least one
+    frame, at most max_frames). Returns (Mpx/s, frames, seconds)."""
     import oracle
     done_px, t0, nfr = 0, time.perf_counter(), 0
-    while nfr < 64:
+    while nfr < max_frames:
         d = frames_np[nfr % len(frames_np)]
         oracle.forward(d, K, alpha=2, stat_mode=oracle.STAT_SECANT, tau=12.0, depth_scale=0.001,
                        nthreads=cores)
@@ -313,11 +332,14 @@ def bench_ours(args, dist: Dist):
     if dist.rank == 0 and not args.skip_cpu:
         cores = cpu_cores()
         frames_np = [depth[i].cpu().numpy() for i in range(min(4, N_FRAMES))]
-        mpx, nfr, dt = time_oracle_on(frames_np, Ks[0], cores)
+        mpx, nfr, dt = time_oracle_on(frames_np, Ks[0], cores, budget_s=10.0)
+        mpx1, nfr1, dt1 = time_oracle_on(frames_np, Ks[0], 1, budget_s=4.0)
         cpu = {"value": round(mpx, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{nfr} full-HD uint16 frames cycling over the first {len(frames_np)} of the batch "
                          f"({nfr * H_FULLHD * W_FULLHD} px), "
-                         f"FP64 direct form, {cores} threads, {dt:.1f} s"}
+                         f"FP64 direct form, {cores} threads, {dt:.1f} s",
+               "single_thread": {"value": round(mpx1, 3), "unit": UNIT, "frames": nfr1, "seconds": round(dt1, 2)},
+               "cpu_model": cpu_model()}
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": dist.world,
@@ -402,6 +424,49 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
         out[f"multiscale_{form}_1to4_batched_hbm_frac"] = round(px * 19 / (ms / 1e3) / 1e9 / measured_peaks()[0], 4)
     mb.sync_status()
     del mb
+    # alpha = 1 (the paper's synthetic-data setting) on the same batch.
+    a1 = nrm.BatchedEstimator(nrm.NormalParams(alpha=1), device=dev)
+    fa1, _ = a1.make_frames([(depth[i], Ks[i]) for i in range(N_FRAMES)],
+                            [(normals[i], valid[i]) for i in range(N_FRAMES)])
+    if not args.no_autotune:
+        a1.autotune([(depth[i], Ks[i]) for i in range(N_FRAMES)], [(normals[i], valid[i]) for i in range(N_FRAMES)])
+    for _ in range(3):
+        a1.run(fa1, N_FRAMES, stream)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        a1.run(fa1, N_FRAMES, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    out["u16_alpha1_mpx_s"] = round(px / (ms / 1e3) / 1e6, 1)
+    out["u16_alpha1_hbm_frac"] = round(px * 19 / (ms / 1e3) / 1e9 / measured_peaks()[0], 4)
+    a1.sync_status()
+    del a1
+
+    # The single 640 x 480 float32 frame, plain per-frame launches, rotating
+    # over 256 input/output sets (1.6 GB, more than 4x L2) so that no frame is
+    # served from L2.
+    d1, k1 = scenes.cfg1_depth(dev)
+    nrot = 256
+    rot_d = d1.unsqueeze(0).repeat(nrot, 1, 1).contiguous()
+    rot_n = torch.empty((nrot, 480, 640, 4), device=dev)
+    rot_v = torch.empty((nrot, 480, 640), dtype=torch.uint8, device=dev)
+    c1 = nrm.NormalEstimator(k1, 480, 640, nrm.NormalParams(), device=dev)
+    for i in range(nrot):
+        c1.estimate(rot_d[i], rot_n[i], rot_v[i], stream)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for r in range(4):
+        for i in range(nrot):
+            c1.estimate(rot_d[i], rot_n[i], rot_v[i], stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / (4 * nrot)
+    out["cfg1_640x480_plain_mpx_s"] = round(480 * 640 / (ms / 1e3) / 1e6, 1)
+    out["cfg1_640x480_plain_us_per_frame"] = round(ms * 1e3, 2)
+    c1.sync_status()
+    del rot_d, rot_n, rot_v, c1
 
     # Half output on the same batch (11 B/px).
     h16 = nrm.BatchedEstimator(nrm.NormalParams(out_dtype="f16"), device=dev)
