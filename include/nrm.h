@@ -258,7 +258,9 @@ NRM_API int nrm_estimate_batched_host(nrm_handle* h, const nrm_frame* frames, in
  * 128 x 16, 256 compute threads). Frames as for nrm_estimate_batched; their
  * points must be NULL (NRM_ERR_UNSUPPORTED otherwise). The per-scale constants
  * are formed on the GPU from each frame's intrinsics, so results can differ
- * from nrm_estimate_multiscale's in the last bits. n = 0 is a no-op. */
+ * from nrm_estimate_multiscale's in the last bits. n = 0 is a no-op. Up to 100
+ * frames the descriptors travel as one kernel parameter, and while the stream
+ * is being captured the call records a single kernel node (then n <= 100). */
 NRM_API int nrm_estimate_batched_multiscale(nrm_handle* h, const nrm_frame* frames, int n, const nrm_scales* scales,
                                             void* cuda_stream);
 

@@ -1235,16 +1235,40 @@ int nrm_estimate_batched_multiscale(nrm_handle* h, const nrm_frame* frames, int 
   }
   if (total == 0) return NRM_OK;
   DeviceGuard guard(h->device);
-  Slot& s = h->slots[h->next_slot];
-  h->next_slot = (h->next_slot + 1) % kSlots;
-  rc = retire_slot(h, s);
-  if (rc) return rc;
-  rc = ensure_slot_capacity(h, s, n);
-  if (rc) return rc;
-  char* base = static_cast<char*>(s.host);
-  nrm::BatchHeader* hdr = reinterpret_cast<nrm::BatchHeader*>(base);
-  int* tb = reinterpret_cast<int*>(base + nrm::kTileBeginOffset);
-  FrameDesc* fd = reinterpret_cast<FrameDesc*>(base + nrm::frames_offset(s.capacity));
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  NRM_CUDA(cudaStreamIsCapturing(st, &capture), "cudaStreamIsCapturing");
+  const bool captured = capture == cudaStreamCaptureStatusActive;
+  // Up to kParamMaxFrames frames (and always during capture) the descriptor
+  // block is one kernel parameter; larger batches upload it into a ring slot.
+  const bool param = n <= nrm::kParamMaxFrames;
+  if (captured && !param)
+    return fail(NRM_ERR_UNSUPPORTED, "at most %d frames per call during stream capture", nrm::kParamMaxFrames);
+  Slot* sp = nullptr;
+  if (!captured) {
+    sp = &h->slots[h->next_slot];
+    h->next_slot = (h->next_slot + 1) % kSlots;
+    NRM_CHECK(retire_slot(h, *sp));
+    if (!param) NRM_CHECK(ensure_slot_capacity(h, *sp, n));
+  }
+  std::vector<FrameDesc> fdv;
+  std::vector<int> tbv;
+  nrm::BatchHeader hdr_local;
+  std::memset(&hdr_local, 0, sizeof(hdr_local));
+  nrm::BatchHeader* hdr = &hdr_local;
+  FrameDesc* fd;
+  int* tb;
+  if (param) {
+    fdv.resize((size_t)n);
+    tbv.resize((size_t)n + 1);
+    fd = fdv.data();
+    tb = tbv.data();
+  } else {
+    char* base = static_cast<char*>(sp->host);
+    hdr = reinterpret_cast<nrm::BatchHeader*>(base);
+    tb = reinterpret_cast<int*>(base + nrm::kTileBeginOffset);
+    fd = reinterpret_cast<FrameDesc*>(base + nrm::frames_offset(sp->capacity));
+  }
   const double q = scales->form == NRM_MS_QUAD ? 4.0 : 1.0;
   int acc = 0;
   for (int i = 0; i < n; ++i) {
@@ -1264,20 +1288,30 @@ int nrm_estimate_batched_multiscale(nrm_handle* h, const nrm_frame* frames, int 
   tb[n] = acc;
   hdr->n_frames = n;
   hdr->total_tiles = acc;
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  const size_t used = nrm::frames_offset(s.capacity) + sizeof(FrameDesc) * (size_t)n;
-  NRM_CUDA(cudaMemcpyAsync(s.dev, s.host, used, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
   nrm::BatchArgs args;
-  args.hdr = reinterpret_cast<const nrm::BatchHeader*>(s.dev);
-  args.tile_begin = reinterpret_cast<const int*>(static_cast<char*>(s.dev) + nrm::kTileBeginOffset);
-  args.frames = reinterpret_cast<const FrameDesc*>(static_cast<char*>(s.dev) + nrm::frames_offset(s.capacity));
+  std::memset(&args, 0, sizeof(args));
   nrm::Globals g = make_globals(h);
-  NRM_CUDA(nrm::launch_multiscale_batched(args, ms, g, h->p.out_dtype, scales->form, acc, u16, st),
-           "launch fwd_ms_persistent_kernel");
-  NRM_CUDA(cudaEventRecord(s.done, st), "cudaEventRecord");
-  s.in_flight = true;
-  s.timed_launch = false;
-  s.tiles = acc;
+  if (param) {
+    std::vector<unsigned char> raw(nrm::param_batch_bytes() + 128);
+    void* pb = raw.data() + (128 - reinterpret_cast<uintptr_t>(raw.data()) % 128) % 128;
+    nrm::pack_param_batch(pb, *hdr, tb, fd, n);
+    NRM_CUDA(nrm::launch_multiscale_batched(args, ms, g, h->p.out_dtype, scales->form, acc, u16, st, pb),
+             "launch fwd_ms_persistent_param_kernel");
+  } else {
+    const size_t used = nrm::frames_offset(sp->capacity) + sizeof(FrameDesc) * (size_t)n;
+    NRM_CUDA(cudaMemcpyAsync(sp->dev, sp->host, used, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    args.hdr = reinterpret_cast<const nrm::BatchHeader*>(sp->dev);
+    args.tile_begin = reinterpret_cast<const int*>(static_cast<char*>(sp->dev) + nrm::kTileBeginOffset);
+    args.frames = reinterpret_cast<const FrameDesc*>(static_cast<char*>(sp->dev) + nrm::frames_offset(sp->capacity));
+    NRM_CUDA(nrm::launch_multiscale_batched(args, ms, g, h->p.out_dtype, scales->form, acc, u16, st),
+             "launch fwd_ms_persistent_kernel");
+  }
+  if (sp) {
+    NRM_CUDA(cudaEventRecord(sp->done, st), "cudaEventRecord");
+    sp->in_flight = true;
+    sp->timed_launch = false;
+    sp->tiles = acc;
+  }
   return NRM_OK;
 }
 

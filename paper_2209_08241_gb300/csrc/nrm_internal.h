@@ -220,8 +220,12 @@ cudaError_t launch_multiscale(const FrameDesc& fd, const MsConsts& ms, const Glo
 // s^2 / (q fx fy K) (s the depth scale, q = 1 for NRM_MS_PAIR and 4 for
 // NRM_MS_QUAD); ms.A, ms.B, ms.C are not used. u16: every frame is uint16.
 constexpr int kMsStages = 3;
+// param_block: a ParamBatch packed by pack_param_batch (batches of at most
+// kParamMaxFrames frames; args' pointers are then unused), or NULL for the
+// device descriptor block in args.
 cudaError_t launch_multiscale_batched(const BatchArgs& args, const MsConsts& ms, const Globals& g, int out_dtype,
-                                      int form, int total_tiles, bool u16, cudaStream_t stream);
+                                      int form, int total_tiles, bool u16, cudaStream_t stream,
+                                      const void* param_block = nullptr);
 
 // Bounded-wait self-test (nrm_selftest.cu): status2 = two device ints (zeroed
 // by the caller), one per wait flavour.

@@ -147,6 +147,40 @@ struct FrameMultiStencil {
   }
 };
 
+// The multi-scale tile: the frame's stencil constants, then the shared epilogue.
+template <int OUT, int FORM>
+__device__ __forceinline__ void ms_tile(const MsConsts& ms, const Globals& g, const float* F, int fw, int pad4,
+                                        const TileFrame& tf, int gx0, int gy0) {
+  const FrameMultiStencil<FORM> st{&ms, tf.a, tf.b, tf.c, fw};
+  const bool full = gx0 + TX <= tf.W;
+  if (g.mask_mode == NRM_MASK_SECANT) {
+    if (full)
+      compute_tile_with<TX, TY, NT, OUT, true, true>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
+    else
+      compute_tile_with<TX, TY, NT, OUT, true, false>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
+  } else {
+    if (full)
+      compute_tile_with<TX, TY, NT, OUT, false, true>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
+    else
+      compute_tile_with<TX, TY, NT, OUT, false, false>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
+  }
+}
+
+// The batch's descriptor block as a kernel parameter (no upload, no fences).
+template <int OUT, int FORM>
+__global__ void __launch_bounds__(NT + 32)
+    fwd_ms_persistent_param_kernel(const __grid_constant__ ParamBatch pb, const BatchArgs ring,
+                                   const __grid_constant__ MsConsts ms, const Globals g) {
+  BatchArgs args = ring;
+  args.hdr = &pb.hdr;
+  args.tile_begin = pb.tile_begin;
+  args.frames = pb.frames;
+  auto compute = [&](const float* F, int fw, int pad4, const TileFrame& tf, int gx0, int gy0) {
+    ms_tile<OUT, FORM>(ms, g, F, fw, pad4, tf, gx0, gy0);
+  };
+  persistent_pipeline<TX, TY, NT, decltype(compute), false>(args, g, compute);
+}
+
 template <int OUT, int FORM>
 __global__ void __launch_bounds__(NT + 32)
     fwd_ms_persistent_kernel(const BatchArgs args, const __grid_constant__ MsConsts ms, const Globals g) {
@@ -166,6 +200,17 @@ __global__ void __launch_bounds__(NT + 32)
             compute_tile_with<TX, TY, NT, OUT, false, false>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
         }
       });
+}
+
+const void* ms_persistent_param_kernel(int out_dtype, int form) {
+  static const void* k[3][2] = {
+      {(const void*)fwd_ms_persistent_param_kernel<NRM_OUT_F32X4, NRM_MS_PAIR>,
+       (const void*)fwd_ms_persistent_param_kernel<NRM_OUT_F32X4, NRM_MS_QUAD>},
+      {(const void*)fwd_ms_persistent_param_kernel<NRM_OUT_F16X4, NRM_MS_PAIR>,
+       (const void*)fwd_ms_persistent_param_kernel<NRM_OUT_F16X4, NRM_MS_QUAD>},
+      {(const void*)fwd_ms_persistent_param_kernel<NRM_OUT_OCT16, NRM_MS_PAIR>,
+       (const void*)fwd_ms_persistent_param_kernel<NRM_OUT_OCT16, NRM_MS_QUAD>}};
+  return k[out_dtype][form];
 }
 
 const void* ms_persistent_kernel(int out_dtype, int form) {
@@ -216,18 +261,20 @@ cudaError_t launch_multiscale(const FrameDesc& fd, const MsConsts& ms, const Glo
 }
 
 cudaError_t launch_multiscale_batched(const BatchArgs& args, const MsConsts& ms, const Globals& g, int out_dtype,
-                                      int form, int total_tiles, bool u16, cudaStream_t stream) {
+                                      int form, int total_tiles, bool u16, cudaStream_t stream,
+                                      const void* param_block) {
   if (out_dtype < 0 || out_dtype > 2 || form < 0 || form > 1) return cudaErrorInvalidValue;
-  const void* fn = ms_persistent_kernel(out_dtype, form);
-  static std::atomic<bool> granted[3][2][64];
+  const bool param = param_block != nullptr;
+  const void* fn = param ? ms_persistent_param_kernel(out_dtype, form) : ms_persistent_kernel(out_dtype, form);
+  static std::atomic<bool> granted[2][3][2][64];
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 63;
-  if (!granted[out_dtype][form][dev].load()) {
+  if (!granted[param][out_dtype][form][dev].load()) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)persistent_smem_bytes(TX, TY, NRM_MAX_ALPHA, kMsStages));
     if (e != cudaSuccess) return e;
-    granted[out_dtype][form][dev].store(true);
+    granted[param][out_dtype][form][dev].store(true);
   }
   const unsigned smem = persistent_smem_bytes(TX, TY, ms.alpha_max, kMsStages, u16 ? 2 : 0);
   int occ = 0;
@@ -244,9 +291,12 @@ cudaError_t launch_multiscale_batched(const BatchArgs& args, const MsConsts& ms,
   MsConsts m = ms;
   Globals gg = g;
   gg.alpha = ms.alpha_max;
+  if (param) {
+    void* pargs[4] = {const_cast<void*>(param_block), &a, &m, &gg};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(persistent_threads(NT)), pargs, smem, stream);
+  }
   void* kargs[3] = {&a, &m, &gg};
-  e = cudaLaunchKernel(fn, dim3(grid), dim3(persistent_threads(NT)), kargs, smem, stream);
-  return e;
+  return cudaLaunchKernel(fn, dim3(grid), dim3(persistent_threads(NT)), kargs, smem, stream);
 }
 
 }  // namespace nrm

@@ -86,3 +86,22 @@ def test_batched_adjoint_captures_and_replays():
     b.sync_status()
     for x, r in zip(grads, ref):
         assert torch.equal(x, r)
+
+
+def test_batched_multiscale_captures_and_replays():
+    items = [scenes.random_frame(2600 + i, 320 + 64 * i, 240, DEV, kind="u16") for i in range(3)]
+    b = nrm.BatchedEstimator()
+    ref = [(n.clone(), m.clone()) for n, m in b.multiscale(items, (1, 2, 3), "quad")]
+    outs = b.multiscale(items, (1, 2, 3), "quad")
+    arr, _ = b.make_frames(items, outs)
+    torch.cuda.synchronize()
+    for n, m in outs:
+        n.zero_()
+        m.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=torch.cuda.Stream()):
+        b.run_multiscale(arr, len(items), (1, 2, 3), "quad", torch.cuda.current_stream())
+    g.replay()
+    torch.cuda.synchronize()
+    for (n, m), (rn, rm) in zip(outs, ref):
+        assert torch.equal(m, rm) and torch.equal(n, rn)

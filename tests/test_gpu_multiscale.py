@@ -175,3 +175,17 @@ def test_batched_multiscale_rejects_point_buffers():
     arr, _ = b.make_frames([(d, K)], [(n, m, P)])
     with pytest.raises(nrm._lib.NrmError):
         b.run_multiscale(arr, 1)
+
+
+def test_batched_multiscale_ring_path_for_large_batches():
+    """More than 100 frames take the device descriptor ring; the results equal
+    those of the same frames in small (parameter-path) batches."""
+    items = [scenes.random_frame(1750 + (i % 7), 96, 64, DEV, kind="u16") for i in range(105)]
+    b = nrm.BatchedEstimator()
+    big = b.multiscale(items, (1, 2), "pair")
+    small = []
+    for k in range(0, 105, 35):
+        small += b.multiscale(items[k:k + 35], (1, 2), "pair")
+    b.sync_status()
+    for (n1, m1), (n2, m2) in zip(big, small):
+        assert torch.equal(m1, m2) and torch.equal(n1, n2)
