@@ -424,6 +424,92 @@ struct QuadStencil {
   }
 };
 
+// Section 3.2 for one pixel pair (tile columns 64 p + lane and 64 p + 32 + lane
+// of the row whose first output element is out_row): from the unnormalised
+// n_x, n_y and P = n . (u1, v1, 1), the statistic in squared form, the mask
+// ballots and the normal (or octahedral code) stores. nu1 = -(u1 of both
+// columns), ku = 1 + u1^2, nv1 = -v1, kv = v1^2, T = tau^2 in both lanes.
+template <int OUT, bool SECANT, bool FULL>
+__device__ __forceinline__ void emit_pair(const TileFrame& f, long long out_row, int p, float2 d1, float2 nx,
+                                          float2 ny, float2 P, float2 nu1, float2 ku, float2 nv1, float2 kv,
+                                          float2 T, float tau2, bool cola, bool colb, uint32_t& ballot_a,
+                                          uint32_t& ballot_b) {
+  const float kFltMin = 1.17549435e-38f;
+  const float2 nz = __ffma2_rn(nu1, nx, __ffma2_rn(nv1, ny, P));
+  const float2 q = __ffma2_rn(nx, nx, __ffma2_rn(ny, ny, __fmul2_rn(nz, nz)));
+  // Section 3.2 mask in squared form; NaN (invalid depth) fails every test.
+  // (Bitwise &: every operand is side-effect free, and no branches.)
+  bool ka = cola & (d1.x == d1.x) & (q.x >= kFltMin);
+  bool kb = colb & (d1.y == d1.y) & (q.y >= kFltMin);
+  if (SECANT) {
+    const float2 lhs = __fmul2_rn(q, __fadd2_rn(ku, kv));
+    const float2 rhs = __fmul2_rn(T, __fmul2_rn(P, P));
+    ka = ka & (lhs.x <= rhs.x);
+    kb = kb & (lhs.y <= rhs.y);
+  } else {
+    ka = ka & (q.x <= tau2);
+    kb = kb & (q.y <= tau2);
+  }
+  ballot_a = __ballot_sync(0xffffffffu, ka);
+  ballot_b = __ballot_sync(0xffffffffu, kb);
+  if (OUT == NRM_OUT_OCT16) {
+    // Octahedral code of n (scale-invariant: n need not be normalised).
+    uint32_t ca, cb;
+    oct16_encode2(nx, ny, nz, ca, cb);
+    ca = ka ? ca : 0u;
+    cb = kb ? cb : 0u;
+    uint32_t* dst = reinterpret_cast<uint32_t*>(f.normals) + out_row + 64 * p;
+    if (FULL || cola) __stcs(dst, ca);
+    if (FULL || colb) __stcs(dst + 32, cb);
+    return;
+  }
+  const float2 inv = f2(rsqrt_ftz(q.x), rsqrt_ftz(q.y));
+  const float2 ox = __fmul2_rn(nx, inv), oy = __fmul2_rn(ny, inv), oz = __fmul2_rn(nz, inv);
+  // Select, not multiply: n is NaN next to invalid depths.
+  const float4 va = ka ? make_float4(ox.x, oy.x, oz.x, 0.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 vb = kb ? make_float4(ox.y, oy.y, oz.y, 0.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
+  if (OUT == NRM_OUT_F16X4) {
+    const __half2 xya = __floats2half2_rn(va.x, va.y), zwa = __floats2half2_rn(va.z, 0.0f);
+    const __half2 xyb = __floats2half2_rn(vb.x, vb.y), zwb = __floats2half2_rn(vb.z, 0.0f);
+    uint2* dst = reinterpret_cast<uint2*>(f.normals) + out_row + 64 * p;
+    if (FULL || cola)
+      __stcs(dst, make_uint2(*reinterpret_cast<const uint32_t*>(&xya), *reinterpret_cast<const uint32_t*>(&zwa)));
+    if (FULL || colb)
+      __stcs(dst + 32, make_uint2(*reinterpret_cast<const uint32_t*>(&xyb), *reinterpret_cast<const uint32_t*>(&zwb)));
+  } else {
+    float4* dst = reinterpret_cast<float4*>(f.normals) + out_row + 64 * p;
+    if (FULL || cola) __stcs(dst, va);
+    if (FULL || colb) __stcs(dst + 32, vb);
+  }
+}
+
+// The mask bytes of one tile row from its CH ballots (ballot c covers tile
+// columns 32 c .. 32 c + 31): lane l writes columns [CH l, CH l + CH).
+template <int CH, bool FULL>
+__device__ __forceinline__ void emit_mask_row(const TileFrame& f, int gx0, int gy, int lane,
+                                              const uint32_t (&ballots)[CH]) {
+  const int first = CH * lane;
+  const int cidx = first >> 5;
+  uint32_t word = 0;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) word = (c == cidx) ? ballots[c] : word;
+  const uint32_t bits = (word >> (first & 31)) & ((1u << CH) - 1u);
+  const int gx = gx0 + first;
+  uint8_t* mrow = f.valid + (long long)gy * f.out_pitch;
+  if ((FULL || gx + CH <= f.W) && f.mask_align >= CH) {
+    if (CH == 2) {
+      __stcs(reinterpret_cast<unsigned short*>(mrow + gx), (unsigned short)bits_to_bytes4(bits));
+    } else {
+      __stcs(reinterpret_cast<unsigned int*>(mrow + gx), bits_to_bytes4(bits));
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      if (gx + j < f.W) mrow[gx + j] = (uint8_t)((bits >> j) & 1u);
+    }
+  }
+}
+
 // Computes one TX x TY output tile from the decoded float halo tile F
 // (origin global (gx0 - padx, gy0 - halo), row pitch bw), threads 0..NT-1,
 // with the stencil st giving each pixel pair's unnormalised normal.
@@ -445,7 +531,6 @@ __device__ __forceinline__ void compute_tile_with(const float* __restrict__ F, i
   static_assert(CH == 2 || CH == 4, "TX must be 64 or 128");
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const float kFltMin = 1.17549435e-38f;
 
   float2 nu1[NP], ku[NP];
   bool colok[CH];
@@ -478,75 +563,10 @@ __device__ __forceinline__ void compute_tile_with(const float* __restrict__ F, i
       const float2 d1 = f2(pa[0], pb[0]);
       float2 nx, ny, P;
       st(pa, pb, d1, nx, ny, P);
-      const float2 nz = __ffma2_rn(nu1[p], nx, __ffma2_rn(nv1, ny, P));
-      const float2 q = __ffma2_rn(nx, nx, __ffma2_rn(ny, ny, __fmul2_rn(nz, nz)));
-      // Section 3.2 mask in squared form; NaN (invalid depth) fails every test.
-      // (Bitwise &: every operand is side-effect free, and no branches.)
-      bool ka = colok[2 * p] & (d1.x == d1.x) & (q.x >= kFltMin);
-      bool kb = colok[2 * p + 1] & (d1.y == d1.y) & (q.y >= kFltMin);
-      if (SECANT) {
-        const float2 lhs = __fmul2_rn(q, __fadd2_rn(ku[p], kv));
-        const float2 rhs = __fmul2_rn(T, __fmul2_rn(P, P));
-        ka = ka & (lhs.x <= rhs.x);
-        kb = kb & (lhs.y <= rhs.y);
-      } else {
-        ka = ka & (q.x <= tau2);
-        kb = kb & (q.y <= tau2);
-      }
-      ballots[2 * p] = __ballot_sync(0xffffffffu, ka);
-      ballots[2 * p + 1] = __ballot_sync(0xffffffffu, kb);
-      if (OUT == NRM_OUT_OCT16) {
-        // Octahedral code of n (scale-invariant: n need not be normalised).
-        uint32_t ca, cb;
-        oct16_encode2(nx, ny, nz, ca, cb);
-        ca = ka ? ca : 0u;
-        cb = kb ? cb : 0u;
-        uint32_t* dst = reinterpret_cast<uint32_t*>(f.normals) + out_row + 64 * p;
-        if (FULL || colok[2 * p]) __stcs(dst, ca);
-        if (FULL || colok[2 * p + 1]) __stcs(dst + 32, cb);
-        continue;
-      }
-      const float2 inv = f2(rsqrt_ftz(q.x), rsqrt_ftz(q.y));
-      const float2 ox = __fmul2_rn(nx, inv), oy = __fmul2_rn(ny, inv), oz = __fmul2_rn(nz, inv);
-      // Select, not multiply: n is NaN next to invalid depths.
-      const float4 va = ka ? make_float4(ox.x, oy.x, oz.x, 0.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 vb = kb ? make_float4(ox.y, oy.y, oz.y, 0.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
-      if (OUT == NRM_OUT_F16X4) {
-        const __half2 xya = __floats2half2_rn(va.x, va.y), zwa = __floats2half2_rn(va.z, 0.0f);
-        const __half2 xyb = __floats2half2_rn(vb.x, vb.y), zwb = __floats2half2_rn(vb.z, 0.0f);
-        uint2* dst = reinterpret_cast<uint2*>(f.normals) + out_row + 64 * p;
-        if (FULL || colok[2 * p])
-          __stcs(dst, make_uint2(*reinterpret_cast<const uint32_t*>(&xya), *reinterpret_cast<const uint32_t*>(&zwa)));
-        if (FULL || colok[2 * p + 1])
-          __stcs(dst + 32,
-                 make_uint2(*reinterpret_cast<const uint32_t*>(&xyb), *reinterpret_cast<const uint32_t*>(&zwb)));
-      } else {
-        float4* dst = reinterpret_cast<float4*>(f.normals) + out_row + 64 * p;
-        if (FULL || colok[2 * p]) __stcs(dst, va);
-        if (FULL || colok[2 * p + 1]) __stcs(dst + 32, vb);
-      }
+      emit_pair<OUT, SECANT, FULL>(f, out_row, p, d1, nx, ny, P, nu1[p], ku[p], nv1, kv, T, tau2, colok[2 * p],
+                                   colok[2 * p + 1], ballots[2 * p], ballots[2 * p + 1]);
     }
-    // Mask: lane l owns tile columns [CH l, CH l + CH).
-    const int first = CH * lane;
-    const int cidx = first >> 5;
-    uint32_t word = 0;
-#pragma unroll
-    for (int c = 0; c < CH; ++c) word = (c == cidx) ? ballots[c] : word;
-    const uint32_t bits = (word >> (first & 31)) & ((1u << CH) - 1u);
-    const int gx = gx0 + first;
-    uint8_t* mrow = f.valid + (long long)gy * f.out_pitch;
-    if ((FULL || gx + CH <= f.W) && f.mask_align >= CH) {
-      if (CH == 2) {
-        __stcs(reinterpret_cast<unsigned short*>(mrow + gx), (unsigned short)bits_to_bytes4(bits));
-      } else {
-        __stcs(reinterpret_cast<unsigned int*>(mrow + gx), bits_to_bytes4(bits));
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < CH; ++j) {
-        if (gx + j < f.W) mrow[gx + j] = (uint8_t)((bits >> j) & 1u);
-      }
-    }
+    emit_mask_row<CH, FULL>(f, gx0, gy, lane, ballots);
   }
   if (POINTS && f.points) {
     // Organised point cloud P = d1 (u1, v1, 1) in metres (Section 2), the

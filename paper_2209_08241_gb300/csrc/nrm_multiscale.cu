@@ -32,44 +32,134 @@ namespace {
 
 constexpr int TX = kMsTileX, TY = kMsTileY, NT = kMsThreads;
 
-template <int FORM>
-struct MultiStencil {
-  const MsConsts* ms;
-  int bw;
-  __device__ __forceinline__ void operator()(const float* pa, const float* pb, float2 d1, float2& nx, float2& ny,
-                                             float2& P) const {
-    const float2 M1 = f2(-1.0f, -1.0f);
-    // -0 is the identity of addition for every operand, +0 included, so the
-    // first scale's fused multiply-add returns its product exactly, signed zero
-    // included (one four-direction scale then equals the single-scale kernel).
-    float2 ax = f2(-0.f, -0.f), ay = f2(-0.f, -0.f), ap = f2(-0.f, -0.f);
+constexpr int kMsCtasPerSm = 3;
+constexpr int NW = NT / 32;
+constexpr int NP = TX / 64;  // pixel pairs per lane and row
+static_assert(TY % NW == 0 && TX % 64 == 0, "tile shape");
+
+// One tile. Warp w handles rows w, w + NW, ... and lane l the pixel pairs
+// (64 p + l, 64 p + 32 + l), as in the single-scale tile; per row the lane
+// keeps the running sums of n_x, n_y and P of its NP pairs and walks the
+// scales once, so each scale's constants and shared-memory offsets are formed
+// once per row rather than once per pixel pair. Consts(i, A, B, C) gives scale
+// i's constants (sign, 1/K and depth scale folded in). -0 is the identity of
+// addition for every operand, +0 included, so the first scale's fused
+// multiply-add returns its product exactly, signed zero included (one
+// four-direction scale then equals the single-scale kernel). The epilogue
+// (statistic, mask, stores) is the single-scale one.
+template <int OUT, int FORM, bool SECANT, bool FULL, class Consts>
+__device__ __forceinline__ void ms_compute(const float* __restrict__ F, int fw, int pad4, const TileFrame& f,
+                                           int gx0, int gy0, int halo, float tau2, int n_scales,
+                                           const int* alphas, const Consts& consts) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const float2 M1 = f2(-1.0f, -1.0f);
+  float2 nu1[NP], ku[NP];
+  bool colok[2 * NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int gxa = gx0 + 64 * p + lane, gxb = gxa + 32;
+    const float ua = ((float)gxa - f.cx) * f.inv_fx;
+    const float ub = ((float)gxb - f.cx) * f.inv_fx;
+    nu1[p] = f2(-ua, -ub);
+    ku[p] = f2(fmaf(ua, ua, 1.0f), fmaf(ub, ub, 1.0f));
+    colok[2 * p] = FULL || gxa < f.W;
+    colok[2 * p + 1] = FULL || gxb < f.W;
+  }
+  const float2 T = f2(tau2, tau2);
+
 #pragma unroll 1
-    for (int i = 0; i < ms->K; ++i) {
-      const int a = ms->alpha[i];
-      const int dv = a * bw;
-      const float2 A = f2(ms->A[i], ms->A[i]), B = f2(ms->B[i], ms->B[i]), C = f2(ms->C[i], ms->C[i]);
-      const float2 d2 = f2(pa[a], pb[a]);
-      const float2 d3 = f2(pa[dv], pb[dv]);
-      if (FORM == NRM_MS_PAIR) {
-        // Eq. 1-3: A = -sign a/(K fy) s^2, B = -sign a/(K fx) s^2, C = sign a^2/(K fx fy) s^2.
-        const float2 D21 = __ffma2_rn(M1, d1, d2), D31 = __ffma2_rn(M1, d1, d3);
-        ax = __ffma2_rn(__fmul2_rn(A, d3), D21, ax);
-        ay = __ffma2_rn(__fmul2_rn(B, d2), D31, ay);
-        ap = __ffma2_rn(__fmul2_rn(C, d2), d3, ap);
-      } else {
-        // Eq. 4-6: A = -sign a/(4 K fy) s^2, B = -sign a/(4 K fx) s^2, C = sign a^2/(4 K fx fy) s^2.
-        const float2 d4 = f2(pa[-a], pb[-a]);
-        const float2 d5 = f2(pa[-dv], pb[-dv]);
-        const float2 S24 = __fadd2_rn(d2, d4), D24 = __ffma2_rn(M1, d4, d2);
-        const float2 S35 = __fadd2_rn(d3, d5), D35 = __ffma2_rn(M1, d5, d3);
-        ax = __ffma2_rn(__fmul2_rn(A, S35), D24, ax);
-        ay = __ffma2_rn(__fmul2_rn(B, S24), D35, ay);
-        ap = __ffma2_rn(__fmul2_rn(C, S24), S35, ap);
+  for (int ly = warp; ly < TY; ly += NW) {
+    const int gy = gy0 + ly;
+    if (gy >= f.H) break;
+    const float* row = F + (ly + halo) * fw + pad4 + lane;
+    float2 d1[NP], ax[NP], ay[NP], ap[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      d1[p] = f2(row[64 * p], row[64 * p + 32]);
+      ax[p] = ay[p] = ap[p] = f2(-0.f, -0.f);
+    }
+#pragma unroll 1
+    for (int i = 0; i < n_scales; ++i) {
+      const int al = alphas[i];
+      const int dv = al * fw;
+      float sa, sb, sc;
+      consts(i, sa, sb, sc);
+      const float2 A = f2(sa, sa), B = f2(sb, sb), C = f2(sc, sc);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const float* pa = row + 64 * p;
+        const float* pb = pa + 32;
+        const float2 d2 = f2(pa[al], pb[al]);
+        const float2 d3 = f2(pa[dv], pb[dv]);
+        if (FORM == NRM_MS_PAIR) {
+          // Eq. 1-3: A = -sign a/(K fy) s^2, B = -sign a/(K fx) s^2, C = sign a^2/(K fx fy) s^2.
+          const float2 D21 = __ffma2_rn(M1, d1[p], d2), D31 = __ffma2_rn(M1, d1[p], d3);
+          ax[p] = __ffma2_rn(__fmul2_rn(A, d3), D21, ax[p]);
+          ay[p] = __ffma2_rn(__fmul2_rn(B, d2), D31, ay[p]);
+          ap[p] = __ffma2_rn(__fmul2_rn(C, d2), d3, ap[p]);
+        } else {
+          // Eq. 4-6: A = -sign a/(4 K fy) s^2, B = -sign a/(4 K fx) s^2, C = sign a^2/(4 K fx fy) s^2.
+          const float2 d4 = f2(pa[-al], pb[-al]);
+          const float2 d5 = f2(pa[-dv], pb[-dv]);
+          const float2 S24 = __fadd2_rn(d2, d4), D24 = __ffma2_rn(M1, d4, d2);
+          const float2 S35 = __fadd2_rn(d3, d5), D35 = __ffma2_rn(M1, d5, d3);
+          ax[p] = __ffma2_rn(__fmul2_rn(A, S35), D24, ax[p]);
+          ay[p] = __ffma2_rn(__fmul2_rn(B, S24), D35, ay[p]);
+          ap[p] = __ffma2_rn(__fmul2_rn(C, S24), S35, ap[p]);
+        }
       }
     }
-    nx = ax;
-    ny = ay;
-    P = ap;
+    const float v1 = ((float)gy - f.cy) * f.inv_fy;
+    const float2 nv1 = f2(-v1, -v1);
+    const float2 kv = f2(v1 * v1, v1 * v1);
+    const long long out_row = (long long)gy * f.out_pitch + gx0 + lane;
+    uint32_t ballots[2 * NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+      emit_pair<OUT, SECANT, FULL>(f, out_row, p, d1[p], ax[p], ay[p], ap[p], nu1[p], ku[p], nv1, kv, T, tau2,
+                                   colok[2 * p], colok[2 * p + 1], ballots[2 * p], ballots[2 * p + 1]);
+    emit_mask_row<2 * NP, FULL>(f, gx0, gy, lane, ballots);
+  }
+}
+
+template <int OUT, int FORM, class Consts>
+__device__ __forceinline__ void ms_tile_any(const MsConsts& ms, const Globals& g, const float* F, int fw, int pad4,
+                                            const TileFrame& tf, int gx0, int gy0, int halo, const Consts& c) {
+  const bool full = gx0 + TX <= tf.W;
+  if (g.mask_mode == NRM_MASK_SECANT) {
+    if (full)
+      ms_compute<OUT, FORM, true, true>(F, fw, pad4, tf, gx0, gy0, halo, g.tau2, ms.K, ms.alpha, c);
+    else
+      ms_compute<OUT, FORM, true, false>(F, fw, pad4, tf, gx0, gy0, halo, g.tau2, ms.K, ms.alpha, c);
+  } else {
+    if (full)
+      ms_compute<OUT, FORM, false, true>(F, fw, pad4, tf, gx0, gy0, halo, g.tau2, ms.K, ms.alpha, c);
+    else
+      ms_compute<OUT, FORM, false, false>(F, fw, pad4, tf, gx0, gy0, halo, g.tau2, ms.K, ms.alpha, c);
+  }
+}
+
+// Single-frame constants: precomputed per scale on the host.
+struct HostScaleConsts {
+  const MsConsts* ms;
+  __device__ __forceinline__ void operator()(int i, float& A, float& B, float& C) const {
+    A = ms->A[i];
+    B = ms->B[i];
+    C = ms->C[i];
+  }
+};
+
+// Per-frame constants of a batch: alpha_i a, alpha_i b, alpha_i^2 c from the
+// frame's (sign-folded) bases.
+struct FrameScaleConsts {
+  const MsConsts* ms;
+  float a, b, c;
+  __device__ __forceinline__ void operator()(int i, float& A, float& B, float& C) const {
+    const float fa = (float)ms->alpha[i];
+    A = fa * a;
+    B = fa * b;
+    C = fa * fa * c;
   }
 };
 
@@ -91,84 +181,19 @@ __global__ void __launch_bounds__(NT)
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SB + ftile_bytes_for(TX, TY, alpha));
   const TileFrame tf = tile_frame(fd, g.sign);
   if (!stage_plain_tile<NT>(smem, F, bar, fd, tf, alpha, padx, bw, bh, pad4, fw, gx0, gy0, g)) return;
-  const MultiStencil<FORM> st{&ms, fw};
-  const bool full = gx0 + TX <= tf.W;
-  if (g.mask_mode == NRM_MASK_SECANT) {
-    if (full)
-      compute_tile_with<TX, TY, NT, OUT, true, true>(F, fw, pad4, tf, gx0, gy0, alpha, g.tau2, st);
-    else
-      compute_tile_with<TX, TY, NT, OUT, true, false>(F, fw, pad4, tf, gx0, gy0, alpha, g.tau2, st);
-  } else {
-    if (full)
-      compute_tile_with<TX, TY, NT, OUT, false, true>(F, fw, pad4, tf, gx0, gy0, alpha, g.tau2, st);
-    else
-      compute_tile_with<TX, TY, NT, OUT, false, false>(F, fw, pad4, tf, gx0, gy0, alpha, g.tau2, st);
-  }
+  ms_tile_any<OUT, FORM>(ms, g, F, fw, pad4, tf, gx0, gy0, alpha, HostScaleConsts{&ms});
 }
 
-// Per-frame form of MultiStencil: the constants of scale i are alpha_i a,
-// alpha_i b, alpha_i^2 c from the frame's (sign-folded) bases.
-template <int FORM>
-struct FrameMultiStencil {
-  const MsConsts* ms;
-  float a, b, c;
-  int bw;
-  __device__ __forceinline__ void operator()(const float* pa, const float* pb, float2 d1, float2& nx, float2& ny,
-                                             float2& P) const {
-    const float2 M1 = f2(-1.0f, -1.0f);
-    float2 ax = f2(-0.f, -0.f), ay = f2(-0.f, -0.f), ap = f2(-0.f, -0.f);
-#pragma unroll 1
-    for (int i = 0; i < ms->K; ++i) {
-      const int al = ms->alpha[i];
-      const int dv = al * bw;
-      const float fa = (float)al;
-      const float sa = fa * a, sb = fa * b, sc = fa * fa * c;
-      const float2 A = f2(sa, sa), B = f2(sb, sb), C = f2(sc, sc);
-      const float2 d2 = f2(pa[al], pb[al]);
-      const float2 d3 = f2(pa[dv], pb[dv]);
-      if (FORM == NRM_MS_PAIR) {
-        const float2 D21 = __ffma2_rn(M1, d1, d2), D31 = __ffma2_rn(M1, d1, d3);
-        ax = __ffma2_rn(__fmul2_rn(A, d3), D21, ax);
-        ay = __ffma2_rn(__fmul2_rn(B, d2), D31, ay);
-        ap = __ffma2_rn(__fmul2_rn(C, d2), d3, ap);
-      } else {
-        const float2 d4 = f2(pa[-al], pb[-al]);
-        const float2 d5 = f2(pa[-dv], pb[-dv]);
-        const float2 S24 = __fadd2_rn(d2, d4), D24 = __ffma2_rn(M1, d4, d2);
-        const float2 S35 = __fadd2_rn(d3, d5), D35 = __ffma2_rn(M1, d5, d3);
-        ax = __ffma2_rn(__fmul2_rn(A, S35), D24, ax);
-        ay = __ffma2_rn(__fmul2_rn(B, S24), D35, ay);
-        ap = __ffma2_rn(__fmul2_rn(C, S24), S35, ap);
-      }
-    }
-    nx = ax;
-    ny = ay;
-    P = ap;
-  }
-};
-
-// The multi-scale tile: the frame's stencil constants, then the shared epilogue.
+// The multi-scale tile of a batch frame.
 template <int OUT, int FORM>
 __device__ __forceinline__ void ms_tile(const MsConsts& ms, const Globals& g, const float* F, int fw, int pad4,
                                         const TileFrame& tf, int gx0, int gy0) {
-  const FrameMultiStencil<FORM> st{&ms, tf.a, tf.b, tf.c, fw};
-  const bool full = gx0 + TX <= tf.W;
-  if (g.mask_mode == NRM_MASK_SECANT) {
-    if (full)
-      compute_tile_with<TX, TY, NT, OUT, true, true>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
-    else
-      compute_tile_with<TX, TY, NT, OUT, true, false>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
-  } else {
-    if (full)
-      compute_tile_with<TX, TY, NT, OUT, false, true>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
-    else
-      compute_tile_with<TX, TY, NT, OUT, false, false>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
-  }
+  ms_tile_any<OUT, FORM>(ms, g, F, fw, pad4, tf, gx0, gy0, g.alpha, FrameScaleConsts{&ms, tf.a, tf.b, tf.c});
 }
 
 // The batch's descriptor block as a kernel parameter (no upload, no fences).
 template <int OUT, int FORM>
-__global__ void __launch_bounds__(NT + 32)
+__global__ void __launch_bounds__(NT + 32, kMsCtasPerSm)
     fwd_ms_persistent_param_kernel(const __grid_constant__ ParamBatch pb, const BatchArgs ring,
                                    const __grid_constant__ MsConsts ms, const Globals g) {
   BatchArgs args = ring;
@@ -182,24 +207,12 @@ __global__ void __launch_bounds__(NT + 32)
 }
 
 template <int OUT, int FORM>
-__global__ void __launch_bounds__(NT + 32)
+__global__ void __launch_bounds__(NT + 32, kMsCtasPerSm)
     fwd_ms_persistent_kernel(const BatchArgs args, const __grid_constant__ MsConsts ms, const Globals g) {
-  persistent_pipeline<TX, TY, NT>(
-      args, g, [&](const float* F, int fw, int pad4, const TileFrame& tf, int gx0, int gy0) {
-        const FrameMultiStencil<FORM> st{&ms, tf.a, tf.b, tf.c, fw};
-        const bool full = gx0 + TX <= tf.W;
-        if (g.mask_mode == NRM_MASK_SECANT) {
-          if (full)
-            compute_tile_with<TX, TY, NT, OUT, true, true>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
-          else
-            compute_tile_with<TX, TY, NT, OUT, true, false>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
-        } else {
-          if (full)
-            compute_tile_with<TX, TY, NT, OUT, false, true>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
-          else
-            compute_tile_with<TX, TY, NT, OUT, false, false>(F, fw, pad4, tf, gx0, gy0, g.alpha, g.tau2, st);
-        }
-      });
+  persistent_pipeline<TX, TY, NT>(args, g,
+                                  [&](const float* F, int fw, int pad4, const TileFrame& tf, int gx0, int gy0) {
+                                    ms_tile<OUT, FORM>(ms, g, F, fw, pad4, tf, gx0, gy0);
+                                  });
 }
 
 const void* ms_persistent_param_kernel(int out_dtype, int form) {
@@ -282,9 +295,10 @@ cudaError_t launch_multiscale_batched(const BatchArgs& args, const MsConsts& ms,
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, persistent_threads(NT), smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
-  // Two CTAs of 256 compute threads per SM: 16 compute warps, the count at
-  // which the single-scale batched kernel writes to HBM fastest.
-  const int grid = std::min(total_tiles, std::min(occ, 2) * sms);
+  // Three CTAs of 256 compute threads per SM (24 compute warps): the K
+  // stencils per pixel make this kernel issue-bound rather than HBM-bound, and
+  // the extra warps hide the shared-memory and arithmetic latencies.
+  const int grid = std::min(total_tiles, std::min(occ, kMsCtasPerSm) * sms);
   BatchArgs a = args;
   a.stages = kMsStages;
   a.stage_bytes = stage_bytes_for(TX, TY, ms.alpha_max, u16 ? 2 : 0);
