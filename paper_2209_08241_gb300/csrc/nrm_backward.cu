@@ -14,7 +14,7 @@
 //   dL/dd_q = w2(q - alpha x) + w4(q + alpha x) + w3(q - alpha y) + w5(q + alpha y),
 // a deterministic gather with no atomics.
 //
-// One CTA per 64 x 16 output tile. Three TMA loads on one mbarrier stage the
+// One CTA per 64 x 32 output tile. Three TMA loads on one mbarrier stage the
 // tile's inputs in shared memory: the depth halo of radius 2 alpha, the upstream
 // gradient of the tile extended by alpha (a 3-D float32 box: 4 components x
 // columns x rows, i.e. float4 per pixel) and the mask of the same region (a

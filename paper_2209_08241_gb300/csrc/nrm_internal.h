@@ -147,7 +147,7 @@ void host_make_forward_desc(FrameDesc* d, const nrm_frame& f, const nrm_params& 
 
 // Backward (adjoint) kernel for float32 depth: output tile and threads.
 constexpr int kBwdTileX = 64;
-constexpr int kBwdTileY = 16;
+constexpr int kBwdTileY = 32;
 constexpr int kBwdThreads = 256;
 // Columns of the mask box to the left of the tile: the TMA box must start on a
 // 16-byte boundary, so the mask halo (alpha <= 16 columns) is read from 16.

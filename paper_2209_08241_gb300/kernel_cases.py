@@ -3,7 +3,8 @@
     python -m paper_2209_08241_gb300.kernel_cases CASE [--reps N] [--frames N]
 
 Cases:
-  forward        batched forward on N full-HD uint16 frames (default 8)
+  forward        batched forward on N full-HD uint16 frames (default 8), normals
+                 stored as --out (f32, f16 or oct16)
   adjoint        single-frame adjoint on a 4096 x 3072 float32 frame
   adjoint_batch  batched adjoint on N 640 x 480 float32 frames (default 32)
   plane_fit      plane-fitting ground truth, radius --radius (default 2), on a
@@ -43,13 +44,16 @@ def _time(fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def case_forward(frames: int, reps: int):
+OUT_BYTES = {"f32": 16, "f16": 8, "oct16": 4}
+
+
+def case_forward(frames: int, reps: int, out: str = "f32"):
     items = [scenes.random_frame(1000 + i, 1920, 1080, "cuda", kind="u16") for i in range(frames)]
-    b = nrm.BatchedEstimator()
+    b = nrm.BatchedEstimator(nrm.NormalParams(out_dtype=out))
     outs = b(items)
     ms = _time(lambda: b(items, outs), reps)
     px = frames * 1920 * 1080
-    return ms, px, px * 19
+    return ms, px, px * (2 + OUT_BYTES[out] + 1)
 
 
 def case_adjoint(reps: int):
@@ -117,9 +121,10 @@ def main(argv=None):
     ap.add_argument("--form", choices=["pair", "quad"], default="pair")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--frames", type=int, default=0)
+    ap.add_argument("--out", choices=sorted(OUT_BYTES), default="f32")
     a = ap.parse_args(argv)
     if a.case == "forward":
-        ms, px, nbytes = case_forward(a.frames or 8, a.reps)
+        ms, px, nbytes = case_forward(a.frames or 8, a.reps, a.out)
     elif a.case == "adjoint":
         ms, px, nbytes = case_adjoint(a.reps)
     elif a.case == "plane_fit":
