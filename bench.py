@@ -346,10 +346,8 @@ def bench_ours(args, dist: Dist):
         "steps": args.steps, "warmup": w, "ms_per_step": round(ms_per_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
         "data": "synthetic (seeded random-primitive scenes, Kinect-style noise, 1 mm quantisation, 2% holes)",
-        "config": {"workload": f"{N_FRAMES} x 1920x1080 uint16 depth (mm) -> float4 normals + uint8 mask, "
-                               "one batched persistent launch per step",
-                   "frames_per_gpu": N_FRAMES, "H": H_FULLHD, "W": W_FULLHD, "alpha": 2,
-                   "mask": "secant tau=12", "compute": "fp32", "out": "f32x4",
+        "config": {**workload_config(N_FRAMES), "launch": "one batched persistent launch per step",
+                   "compute": "fp32", "out": "f32x4",
                    "tile": f"{tile['tile_x']}x{tile['tile_y']}, {tile['threads']}+32 threads, "
                            f"{tile['stages']} stages"
                            + (f", {tile['ctas_per_sm']} CTAs/SM" if tile.get("ctas_per_sm") else "")
@@ -810,6 +808,13 @@ def bench_serving(args, dev, rates, seconds):
     return res
 
 
+def workload_config(frames: int) -> dict:
+    """The workload both arms are measured on (the reference arm times a
+    bounded sample of it per step and says so in its cpu_baseline)."""
+    return {"workload": f"{frames} x 1920x1080 uint16 depth (mm) -> float4 normals + uint8 mask",
+            "frames_per_gpu": frames, "H": H_FULLHD, "W": W_FULLHD, "alpha": 2, "mask": "secant tau=12"}
+
+
 def bench_reference(args, dist: Dist):
     """The FP64 CPU oracle on this host's cores, on the same workload (frames of
     the same full-HD uint16 batch), each step a bounded sample."""
@@ -848,8 +853,7 @@ def bench_reference(args, dist: Dist):
         "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "64 x 1920x1080 uint16 depth (mm) -> normals + mask (bounded sample per step)",
-                   "alpha": 2, "mask": "secant tau=12"},
+        "config": {**workload_config(args.frames), "compute": "fp64 (oracle)"},
         "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -57,3 +57,6 @@ def test_reference_arm_under_torchrun_prints_once():
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["value"] > 0
     assert rec["e2e"]["h2d_bytes_per_step"] == 0 and rec["cpu_baseline"]["kind"] == "oracle"
+    # Same workload description as the GPU arm's line.
+    import bench
+    assert {k: rec["config"][k] for k in bench.workload_config(64)} == bench.workload_config(64)
