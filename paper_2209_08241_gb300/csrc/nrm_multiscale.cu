@@ -9,16 +9,18 @@
 // The unnormalised per-scale vectors are averaged (the 1/K, the depth scale^2
 // and the orientation sign are folded into per-scale constants), then the
 // Section 3.2 statistic, mask and stores are those of the single-scale kernel
-// (compute_tile_with). Both stencils give n_z = -u1 n_x - v1 n_y + n . ray, so
-// only n_x, n_y and n . ray are accumulated.
+// (emit_pair, emit_mask_row). Both stencils give n_z = -u1 n_x - v1 n_y +
+// n . ray, so only n_x, n_y and n . ray are accumulated.
 //
 // fwd_ms_kernel: one CTA per 128 x 16 tile of one frame, with a halo of the
 // largest scale, staged by TMA (or plain loads) and decoded once; the
 // per-pixel work is K stencil evaluations from shared memory.
-// fwd_ms_persistent_kernel: the batched form, on the persistent pipeline of
-// the single-scale batched kernel (producer warp, TMA stage ring); each
-// frame's descriptor carries its base constants a, b, c (see
-// launch_multiscale_batched), scaled per scale by alpha_i and alpha_i^2.
+// fwd_ms_persistent_kernel / fwd_ms_persistent_param_kernel: the batched
+// form, on the persistent pipeline of the single-scale batched kernel
+// (producer warp, TMA stage ring), with the descriptor block in global memory
+// or as the kernel parameter; each frame's descriptor carries its base
+// constants a, b, c (see launch_multiscale_batched), scaled per scale by
+// alpha_i and alpha_i^2.
 #include <algorithm>
 #include <atomic>
 
