@@ -134,7 +134,10 @@ NRM_API void nrm_destroy(nrm_handle* h);
 
 /* Single frame, one plain launch (one CTA per tile, TMA-staged halo tiles).
  * depth: H x W (dense, pitch W) of the handle's in_dtype; normals: H x W x 4
- * (dense) of the handle's out_dtype; valid: H x W bytes (dense). */
+ * (dense) of the handle's out_dtype; valid: H x W bytes (dense).
+ * Sizes: H and W up to 2^24 (NRM_ERR_UNSUPPORTED above). A frame with more
+ * tile rows than one launch grid holds (65535) runs as a one-frame
+ * nrm_estimate_batched call, whose results are bitwise the same. */
 NRM_API int nrm_estimate(nrm_handle* h, const void* depth, void* normals, uint8_t* valid,
                  void* cuda_stream);
 
@@ -170,7 +173,8 @@ NRM_API int nrm_estimate_batched(nrm_handle* h, const nrm_frame* frames, int n, 
  * valid: the mask nrm_estimate produced for this depth (a pixel it marks valid
  * must have a positive finite five-point stencil; other masks give undefined
  * gradients). Deterministic (gather, no atomics).
- * Returns NRM_ERR_UNSUPPORTED for a uint16 handle. */
+ * Returns NRM_ERR_UNSUPPORTED for a uint16 handle. A frame with more than 65535
+ * tile rows runs as a one-frame nrm_backward_batched call (same results). */
 NRM_API int nrm_backward(nrm_handle* h, const void* depth, const float* grad_normals,
                  const uint8_t* valid, float* grad_depth, void* cuda_stream);
 
@@ -193,7 +197,8 @@ typedef struct {
  * per-pixel arithmetic as nrm_backward. n = 0 is a no-op. Up to 60 frames the
  * frame records and tensor maps travel as one kernel parameter (nothing to
  * upload; the call can be recorded by stream capture); larger batches use a
- * ring of device descriptor blocks. */
+ * ring of device descriptor blocks and return NRM_ERR_UNSUPPORTED while the
+ * stream is being captured. */
 NRM_API int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, void* cuda_stream);
 
 /* Spherical angle images of a normal map (Section 4, the I_phi and I_theta
@@ -227,7 +232,9 @@ NRM_API int nrm_angle_mse(nrm_handle* h, const float* normals, const uint8_t* va
  * depth dtype, depth scale, output dtype and orientation apply; its alpha is
  * ignored. A pixel is valid only if every depth that any scale uses is inside
  * the image and valid. Buffers as for nrm_estimate (device pointers, pitch W,
- * asynchronous on the stream). */
+ * asynchronous on the stream). A frame with more than 65535 tile rows runs as a
+ * one-frame nrm_estimate_batched_multiscale call (whose per-scale constants
+ * are formed on the GPU, so results can differ in the last bits). */
 #define NRM_MAX_SCALES 8
 typedef enum { NRM_MS_PAIR = 0, NRM_MS_QUAD = 1 } nrm_ms_form;
 typedef struct {
@@ -278,7 +285,8 @@ NRM_API int nrm_estimate_batched_multiscale(nrm_handle* h, const nrm_frame* fram
  * normals: H x W x 4 float32 (w = 0), 16-byte aligned; valid: H x W bytes.
  * Device pointers, asynchronous on the stream. radius in 1..NRM_MAX_PLANE_RADIUS,
  * else NRM_ERR_UNSUPPORTED. FP32 arithmetic on coordinates taken relative to the
- * window's centre point; the eigenproblem by cyclic Jacobi rotations. */
+ * window's centre point; the eigenproblem by cyclic Jacobi rotations. One CTA
+ * per 32 x 8 tile: H above 65535 x 8 rows is NRM_ERR_UNSUPPORTED. */
 #define NRM_MAX_PLANE_RADIUS 4
 NRM_API int nrm_plane_fit(nrm_handle* h, const void* depth, float* normals, uint8_t* valid, int radius,
                           void* cuda_stream);

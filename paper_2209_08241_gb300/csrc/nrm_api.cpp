@@ -739,7 +739,9 @@ static int estimate_single(nrm_handle* h, const void* depth, void* normals, uint
             TX + 2 * nrm::pad_x(h->p.alpha, eb), TY + 2 * h->p.alpha, points);
   nrm::Globals g = make_globals(h);
   dim3 grid((f.W + TX - 1) / TX, (f.H + TY - 1) / TY);
-  if (grid.y > 65535) return fail(NRM_ERR_UNSUPPORTED, "too many tile rows for a plain launch");
+  // More tile rows than a launch grid holds: the frame runs as a one-frame
+  // batch (the persistent kernel walks a tile list; same per-pixel code).
+  if (grid.y > 65535) return nrm_estimate_batched(h, &f, 1, cuda_stream);
   void* args[2] = {&d, &g};
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   NRM_CUDA(cudaLaunchKernel(points ? h->pts_plain : h->ks->plain[h->p.out_dtype], grid, dim3(h->cfg.threads),
@@ -1047,8 +1049,21 @@ int nrm_backward(nrm_handle* h, const void* depth, const float* grad_normals, co
   nrm::BwdMaps maps;
   make_bwd_desc(&d, &maps, static_cast<const float*>(depth), grad_normals, valid, grad_depth, h->H, h->W, h->W,
                 h->W, h->K, h->p);
-  if ((h->H + nrm::kBwdTileY - 1) / nrm::kBwdTileY > 65535)
-    return fail(NRM_ERR_UNSUPPORTED, "too many tile rows for the backward launch");
+  if ((h->H + nrm::kBwdTileY - 1) / nrm::kBwdTileY > 65535) {
+    // More tile rows than a launch grid holds: a one-frame batched adjoint
+    // (one grid row of all the frame's tiles; same per-tile code).
+    nrm_grad_frame gf = {};
+    gf.depth = static_cast<const float*>(depth);
+    gf.grad_normals = grad_normals;
+    gf.valid = valid;
+    gf.grad_depth = grad_depth;
+    gf.H = h->H;
+    gf.W = h->W;
+    gf.depth_pitch = h->W;
+    gf.out_pitch = h->W;
+    gf.K = h->K;
+    return nrm_backward_batched(h, &gf, 1, cuda_stream);
+  }
   nrm::Globals g = make_globals(h);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   NRM_CUDA(nrm::launch_backward(d, maps, g, st), "launch bwd_kernel");
@@ -1082,6 +1097,15 @@ int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, voi
   }
   if (total == 0) return NRM_OK;
   DeviceGuard guard(h->device);
+  if (n > nrm::kBwdParamMaxFrames) {
+    // The descriptor ring is uploaded from host memory that later calls reuse:
+    // a captured upload would replay stale or freed host memory.
+    cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+    NRM_CUDA(cudaStreamIsCapturing(static_cast<cudaStream_t>(cuda_stream), &capture), "cudaStreamIsCapturing");
+    if (capture == cudaStreamCaptureStatusActive)
+      return fail(NRM_ERR_UNSUPPORTED, "at most %d frames per batched adjoint during stream capture",
+                  nrm::kBwdParamMaxFrames);
+  }
   if (n <= nrm::kBwdParamMaxFrames) {
     // Small batches: records and tensor maps as one kernel parameter (no
     // upload, no ring slot, no tensor-map fences; also capture-safe).
@@ -1337,8 +1361,9 @@ int nrm_estimate_multiscale(nrm_handle* h, const void* depth, void* normals, uin
   int rc = validate_frame(f, 0, h->p.out_dtype);
   if (rc) return rc;
   if ((long long)f.H * f.W == 0) return NRM_OK;
+  // More tile rows than a launch grid holds: a one-frame batched call.
   if ((f.H + nrm::kMsTileY - 1) / nrm::kMsTileY > 65535)
-    return fail(NRM_ERR_UNSUPPORTED, "too many tile rows for the multi-scale launch");
+    return nrm_estimate_batched_multiscale(h, &f, 1, scales, cuda_stream);
   // Per-scale constants in FP64, rounded once, with 1/K, the depth scale^2 and
   // the orientation sign folded in (Eq. 1-3 or Eq. 4-6). The products are
   // formed in the order of the single-scale constants, so one NRM_MS_QUAD

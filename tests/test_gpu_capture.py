@@ -62,6 +62,26 @@ def test_capture_limits_are_reported():
         with torch.cuda.graph(g, stream=torch.cuda.Stream()):
             b.run(arr, len(items), torch.cuda.current_stream())
     torch.cuda.synchronize()
+    # The same limit for the batched multi-scale forward (100 frames) ...
+    outs = b.multiscale(items, (1, 2), "pair")
+    marr, _ = b.make_frames(items, outs)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with pytest.raises(nrm._lib.NrmError):
+        with torch.cuda.graph(g, stream=torch.cuda.Stream()):
+            b.run_multiscale(marr, len(items), (1, 2), "pair", torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    # ... and for the batched adjoint (60 frames).
+    gitems = items[:61]
+    gs = [torch.zeros_like(n) for n, _ in outs[:61]]
+    grads = [torch.empty_like(d) for d, _ in gitems]
+    garr, _ = b.make_grad_frames(gitems, gs, [m for _, m in outs[:61]], grads)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with pytest.raises(nrm._lib.NrmError):
+        with torch.cuda.graph(g, stream=torch.cuda.Stream()):
+            b.run_backward(garr, len(gitems), torch.cuda.current_stream())
+    torch.cuda.synchronize()
 
 
 def test_batched_adjoint_captures_and_replays():
