@@ -463,8 +463,26 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
     ms = e0.elapsed_time(e1) / (4 * nrot)
     out["cfg1_640x480_plain_mpx_s"] = round(480 * 640 / (ms / 1e3) / 1e6, 1)
     out["cfg1_640x480_plain_us_per_frame"] = round(ms * 1e3, 2)
+    # The same 256 single-frame launches captured once in a CUDA graph and
+    # replayed: the GPU-side cost per frame without the host call path.
+    g1 = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(dev)
+    with torch.cuda.graph(g1, stream=cap):
+        for i in range(nrot):
+            c1.estimate(rot_d[i], rot_n[i], rot_v[i], cap)
+    with torch.cuda.stream(stream):
+        g1.replay()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for r in range(4):
+            g1.replay()
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / (4 * nrot)
+    out["cfg1_640x480_graph_mpx_s"] = round(480 * 640 / (ms / 1e3) / 1e6, 1)
+    out["cfg1_640x480_graph_us_per_frame"] = round(ms * 1e3, 2)
     c1.sync_status()
-    del rot_d, rot_n, rot_v, c1
+    del g1, rot_d, rot_n, rot_v, c1
 
     # Half output on the same batch (11 B/px).
     h16 = nrm.BatchedEstimator(nrm.NormalParams(out_dtype="f16"), device=dev)

@@ -100,9 +100,20 @@ def _intr(K) -> _lib.Intrinsics:
     return _lib.Intrinsics(fx, fy, cx, cy)
 
 
-def _check_cuda(t: torch.Tensor, name: str):
+def _check_cuda(t: torch.Tensor, name: str, device: torch.device | None = None):
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+
+
+def _check_dense(t: torch.Tensor, shape, dtype: torch.dtype, device: torch.device, name: str):
+    """t must be a contiguous CUDA tensor of exactly this shape and dtype on
+    ``device``: the library writes through its raw pointer."""
+    _check_cuda(t, name, device)
+    if tuple(t.shape) != tuple(shape) or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {tuple(shape)} {dtype} tensor, got "
+                         f"{tuple(t.shape)} {t.dtype}{'' if t.is_contiguous() else ' (not contiguous)'}")
 
 
 class _Handle:
@@ -174,20 +185,31 @@ class NormalEstimator(_Handle):
         m = torch.empty((self.H, self.W), dtype=torch.uint8, device=self.device)
         return n, m
 
+    def _check_depth(self, depth: torch.Tensor):
+        _check_cuda(depth, "depth", self.device)
+        if tuple(depth.shape) != (self.H, self.W) or not depth.is_contiguous():
+            raise ValueError(f"depth must be a contiguous ({self.H}, {self.W}) tensor")
+        if _in_dtype(depth) != self.in_dtype:
+            raise TypeError("depth dtype does not match the estimator's in_dtype")
+
+    def _outputs(self, normals: torch.Tensor | None, valid: torch.Tensor | None):
+        """The caller's (normals, valid), checked, or new ones."""
+        if normals is None or valid is None:
+            return self.new_outputs()
+        _check_dense(normals, (self.H, self.W, self.params.out_channels), self.params.torch_out_dtype, self.device,
+                     "normals")
+        _check_dense(valid, (self.H, self.W), torch.uint8, self.device, "valid")
+        return normals, valid
+
     def estimate(self, depth: torch.Tensor, normals: torch.Tensor | None = None,
                  valid: torch.Tensor | None = None, stream=None, points: torch.Tensor | None = None):
         """Writes the (H, W, 4) normal map and (H, W) uint8 mask; returns both.
         With ``points`` ((H, W, 4) float32) the organised point cloud is written
         in the same pass."""
-        _check_cuda(depth, "depth")
-        if tuple(depth.shape) != (self.H, self.W) or not depth.is_contiguous():
-            raise ValueError(f"depth must be a contiguous ({self.H}, {self.W}) tensor")
-        if _in_dtype(depth) != self.in_dtype:
-            raise TypeError("depth dtype does not match the estimator's in_dtype")
-        if normals is None or valid is None:
-            normals, valid = self.new_outputs()
+        self._check_depth(depth)
+        normals, valid = self._outputs(normals, valid)
         if points is not None:
-            _check_points(points, self.H, self.W, self.W)
+            _check_dense(points, (self.H, self.W, 4), torch.float32, self.device, "points")
             _lib.check(self.lib.nrm_estimate_points(self.h, depth.data_ptr(), normals.data_ptr(), valid.data_ptr(),
                                                     points.data_ptr(), _stream_ptr(stream)), "nrm_estimate_points")
             return normals, valid
@@ -200,14 +222,14 @@ class NormalEstimator(_Handle):
     def backward(self, depth: torch.Tensor, grad_normals: torch.Tensor, valid: torch.Tensor,
                  grad_depth: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """dL/d(depth) for upstream dL/d(normals) (H, W, 4) float32, mask fixed."""
-        for t, n in ((depth, "depth"), (grad_normals, "grad_normals"), (valid, "valid")):
-            _check_cuda(t, n)
-            if not t.is_contiguous():
-                raise ValueError(f"{n} must be contiguous")
-        if grad_normals.dtype != torch.float32 or tuple(grad_normals.shape) != (self.H, self.W, 4):
-            raise ValueError("grad_normals must be (H, W, 4) float32")
+        # (A uint16 handle passes here; the library refuses it: NRM_ERR_UNSUPPORTED.)
+        _check_dense(depth, (self.H, self.W), torch.float32 if self.in_dtype == NRM_IN_F32_M else torch.uint16,
+                     self.device, "depth")
+        _check_dense(grad_normals, (self.H, self.W, 4), torch.float32, self.device, "grad_normals")
+        _check_dense(valid, (self.H, self.W), torch.uint8, self.device, "valid")
         if grad_depth is None:
             grad_depth = torch.empty((self.H, self.W), dtype=torch.float32, device=self.device)
+        _check_dense(grad_depth, (self.H, self.W), torch.float32, self.device, "grad_depth")
         _lib.check(self.lib.nrm_backward(self.h, depth.data_ptr(), grad_normals.data_ptr(),
                                          valid.data_ptr(), grad_depth.data_ptr(),
                                          _stream_ptr(stream)), "nrm_backward")
@@ -220,14 +242,9 @@ class NormalEstimator(_Handle):
         each scale the previous method's single pair (``form="pair"``, Eq. 1-3)
         or the four-direction form (``form="quad"``, Eq. 4-6); mask, dtypes and
         orientation as for ``estimate``."""
-        _check_cuda(depth, "depth")
-        if tuple(depth.shape) != (self.H, self.W) or not depth.is_contiguous():
-            raise ValueError(f"depth must be a contiguous ({self.H}, {self.W}) tensor")
-        if _in_dtype(depth) != self.in_dtype:
-            raise TypeError("depth dtype does not match the estimator's in_dtype")
+        self._check_depth(depth)
         sc = _scales(alphas, form)
-        if normals is None or valid is None:
-            normals, valid = self.new_outputs()
+        normals, valid = self._outputs(normals, valid)
         _lib.check(self.lib.nrm_estimate_multiscale(self.h, depth.data_ptr(), normals.data_ptr(), valid.data_ptr(),
                                                     ctypes.byref(sc), _stream_ptr(stream)), "nrm_estimate_multiscale")
         return normals, valid
@@ -237,19 +254,13 @@ class NormalEstimator(_Handle):
         """Plane-fitting ground truth (Sections 1 and 4; radius 2 = 25 points):
         (H, W, 4) float32 normals (w = 0) and (H, W) uint8 mask of the
         (2 radius + 1)^2 window fit, oriented like the method's normals."""
-        _check_cuda(depth, "depth")
-        if tuple(depth.shape) != (self.H, self.W) or not depth.is_contiguous():
-            raise ValueError(f"depth must be a contiguous ({self.H}, {self.W}) tensor")
-        if _in_dtype(depth) != self.in_dtype:
-            raise TypeError("depth dtype does not match the estimator's in_dtype")
+        self._check_depth(depth)
         if normals is None:
             normals = torch.empty((self.H, self.W, 4), dtype=torch.float32, device=self.device)
         if valid is None:
             valid = torch.empty((self.H, self.W), dtype=torch.uint8, device=self.device)
-        if normals.dtype != torch.float32 or tuple(normals.shape) != (self.H, self.W, 4) \
-                or not normals.is_contiguous() or tuple(valid.shape) != (self.H, self.W) \
-                or valid.dtype != torch.uint8 or not valid.is_contiguous():
-            raise ValueError("outputs must be contiguous (H, W, 4) float32 and (H, W) uint8")
+        _check_dense(normals, (self.H, self.W, 4), torch.float32, self.device, "normals")
+        _check_dense(valid, (self.H, self.W), torch.uint8, self.device, "valid")
         _lib.check(self.lib.nrm_plane_fit(self.h, depth.data_ptr(), normals.data_ptr(), valid.data_ptr(),
                                           int(radius), _stream_ptr(stream)), "nrm_plane_fit")
         return normals, valid
@@ -314,7 +325,7 @@ class BatchedEstimator(_Handle):
         arr = (_lib.Frame * max(n, 1))()
         outs = []
         for i, (depth, K) in enumerate(items):
-            _check_cuda(depth, "depth")
+            _check_cuda(depth, "depth", self.device)
             if depth.dim() != 2 or depth.stride(1) != 1:
                 raise ValueError("each depth must be a 2-D tensor with unit column stride")
             H, W = depth.shape
@@ -329,6 +340,8 @@ class BatchedEstimator(_Handle):
                 nm, vm, pm = outputs[i]
             else:
                 nm, vm = outputs[i]
+            for t, name in ((nm, "normals"), (vm, "valid")) + (((pm, "points"),) if pm is not None else ()):
+                _check_cuda(t, name, self.device)
             if tuple(nm.shape) != (H, W, C) or tuple(vm.shape) != (H, W):
                 raise ValueError(f"outputs must be (H, W, {C}) normals and (H, W) valid")
             if depth.numel() and (nm.stride(2) != 1 or nm.stride(1) != C or nm.stride(0) % C
@@ -420,14 +433,17 @@ class BatchedEstimator(_Handle):
         for i, (depth, K) in enumerate(items):
             g, v = grad_normals[i], valids[i]
             for t, name in ((depth, "depth"), (g, "grad_normals"), (v, "valid")):
-                _check_cuda(t, name)
+                _check_cuda(t, name, self.device)
             if depth.dtype != torch.float32 or g.dtype != torch.float32:
                 raise TypeError("the adjoint needs float32 depth and float32 grad_normals")
             H, W = depth.shape
             gd = (torch.empty((H, W), dtype=torch.float32, device=depth.device) if grad_depths is None
                   else grad_depths[i])
+            _check_cuda(gd, "grad_depth", self.device)
             if tuple(g.shape) != (H, W, 4) or tuple(v.shape) != (H, W) or tuple(gd.shape) != (H, W):
                 raise ValueError("shape mismatch in the adjoint batch")
+            if v.dtype != torch.uint8 or gd.dtype != torch.float32:
+                raise TypeError("the adjoint needs a uint8 mask and a float32 grad_depth")
             if depth.numel() and (depth.stride(1) != 1 or gd.stride(1) != 1 or gd.stride(0) != depth.stride(0)
                                   or g.stride(2) != 1 or g.stride(1) != 4 or v.stride(1) != 1
                                   or v.stride(0) * 4 != g.stride(0)):
@@ -514,9 +530,9 @@ class NormalsBatchFunction(torch.autograd.Function):
         return grad, None, None
 
 
-def _check_map(n: torch.Tensor, v: torch.Tensor, name: str):
-    _check_cuda(n, name)
-    _check_cuda(v, name + " mask")
+def _check_map(n: torch.Tensor, v: torch.Tensor, name: str, device: torch.device | None = None):
+    _check_cuda(n, name, device)
+    _check_cuda(v, name + " mask", n.device)
     if n.dtype != torch.float32 or n.dim() != 3 or n.shape[2] != 4 or v.dtype != torch.uint8:
         raise TypeError(f"{name}: expected (H, W, 4) float32 normals and an (H, W) uint8 mask")
     if tuple(v.shape) != tuple(n.shape[:2]) or n.stride(2) != 1 or n.stride(1) != 4 or v.stride(1) != 1 \
@@ -543,8 +559,8 @@ def spherical_images(normals: torch.Tensor, valid: torch.Tensor, stream=None):
 def angle_mse(est, normals, valid, ref_normals, ref_valid, stream=None) -> torch.Tensor:
     """(MSE of I_theta, MSE of I_phi, count) as a float64 CUDA tensor of 3, over
     the pixels valid in both maps (Tables 2-5); ``est`` provides the scratch."""
-    _check_map(normals, valid, "normals")
-    _check_map(ref_normals, ref_valid, "ref_normals")
+    _check_map(normals, valid, "normals", est.device)
+    _check_map(ref_normals, ref_valid, "ref_normals", est.device)
     if valid.shape != ref_valid.shape or valid.stride(0) != ref_valid.stride(0):
         raise ValueError("the two maps must have one shape and pitch")
     out = torch.zeros(3, dtype=torch.float64, device=normals.device)
