@@ -142,3 +142,17 @@ def test_no_device_is_reported_not_hidden():
     rc, h = _create(lib)
     assert rc == _lib.NRM_ERR_NO_DEVICE
     assert not h.value
+
+
+def test_binding_refuses_tensors_the_library_cannot_write():
+    """The binding's tensor check (it runs before every call that passes a raw
+    pointer): host tensors, another device, wrong shape, dtype or layout."""
+    import torch
+
+    import paper_2209_08241_gb300 as nrm
+
+    dev = torch.device("cuda", 0)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        nrm._check_dense(torch.empty((2, 3)), (2, 3), torch.float32, dev, "x")
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        nrm._check_cuda(torch.empty((2, 3), dtype=torch.uint8), "mask", dev)
