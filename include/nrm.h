@@ -30,7 +30,10 @@
  *     orient_to_camera = 1 negates it.
  *
  * Memory and ownership: every depth, normal, mask and gradient pointer passed
- * to this library is a DEVICE pointer owned by the caller. Normals are stored
+ * to this library is a DEVICE pointer owned by the caller (except in
+ * nrm_estimate_batched_host, which takes host pointers). The library cannot
+ * see the extent of a buffer: each must hold the pixels its size and pitch
+ * describe. Normals are stored
  * as 4 components per pixel (x, y, z, 0): float32 (16 B/px) or IEEE half
  * (8 B/px). The mask is one uint8 per pixel. All images are row-major.
  * A handle owns only small device state: per-frame descriptors and TMA tensor
