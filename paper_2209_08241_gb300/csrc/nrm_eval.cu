@@ -32,8 +32,12 @@ __global__ void __launch_bounds__(kThreads)
   if (x >= W) return;
   for (int y = blockIdx.y; y < H; y += gridDim.y) {
     const long long o = (long long)y * pitch + x;
+    // Both loads are issued before the mask is tested (one memory latency,
+    // not two in a row); a masked pixel's stored normal is (0, 0, 0, 0).
+    const uint8_t v = __ldg(valid + o);
+    const float4 nn = __ldg(n + o);
     float p = 0.0f, t = 0.0f;
-    if (__ldg(valid + o)) angles(__ldg(n + o), p, t);
+    if (v) angles(nn, p, t);
     __stcs(phi + o, p);
     __stcs(theta + o, t);
   }
@@ -78,13 +82,20 @@ __global__ void __launch_bounds__(kThreads)
   // final pass add the per-thread sums in FP64.
   float st = 0.0f, sp = 0.0f;
   int cnt = 0;
+  // All four loads of a pixel are independent of the masks, and the loop is
+  // unrolled, so several pixels' loads are in flight before the first mask
+  // test; the sums still run over the pixels in the same order.
   for (int y = blockIdx.x; y < H; y += gridDim.x) {
+    const long long row = (long long)y * pitch;
+#pragma unroll 4
     for (int x = threadIdx.x; x < W; x += kThreads) {
-      const long long o = (long long)y * pitch + x;
-      if (__ldg(va + o) && __ldg(vb + o)) {
+      const long long o = row + x;
+      const uint8_t a = __ldg(va + o), b = __ldg(vb + o);
+      const float4 ma = __ldg(na + o), mb = __ldg(nb + o);
+      if (a && b) {
         float pa, ta, pb, tb;
-        angles(__ldg(na + o), pa, ta);
-        angles(__ldg(nb + o), pb, tb);
+        angles(ma, pa, ta);
+        angles(mb, pb, tb);
         const float dt = ta - tb, dp = pa - pb;
         st = fmaf(dt, dt, st);
         sp = fmaf(dp, dp, sp);

@@ -189,7 +189,7 @@ cudaError_t launch_backward_batched_param(const FrameDesc* frames, const BwdMaps
                                           const Globals& g, cudaStream_t stream);
 
 // Evaluation kernels (nrm_eval.cu).
-constexpr int kMseBlocks = 1024;  // fixed, so that the reduction order never changes
+constexpr int kMseBlocks = 2048;  // fixed, so that the reduction order never changes
 cudaError_t launch_spherical(const float* normals, const uint8_t* valid, int H, int W, long long pitch, float* phi,
                              float* theta, cudaStream_t stream);
 // partials: 3 kMseBlocks doubles of device scratch; out: 3 doubles.

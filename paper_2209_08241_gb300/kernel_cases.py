@@ -12,6 +12,8 @@ Cases:
   multiscale     multi-scale variant, scales 1..4, stencil --form (pair or
                  quad), on a 4096 x 3072 float32 frame
   multiscale_batch  the same, batched, on N full-HD uint16 frames (default 8)
+  spherical      I_phi / I_theta images of a 4096 x 3072 normal map
+  angle_mse      angle-image MSE of two 4096 x 3072 normal maps
 
 Each case runs the kernel ``--reps`` times after one untimed call and prints the
 mean time per call (CUDA events) and the algorithmic bandwidth.
@@ -94,6 +96,24 @@ def case_plane_fit(radius: int, reps: int):
     return ms, px, px * 21
 
 
+def case_spherical(reps: int):
+    d, K = scenes.random_frame(4999, 4096, 3072, "cuda", kind="f32", holes=False, clip_range=False)
+    n, m = nrm.NormalEstimator(K, 3072, 4096)(d)
+    ms = _time(lambda: nrm.spherical_images(n, m), reps)
+    px = 4096 * 3072
+    return ms, px, px * 25
+
+
+def case_angle_mse(reps: int):
+    d, K = scenes.random_frame(4999, 4096, 3072, "cuda", kind="f32", holes=False, clip_range=False)
+    est = nrm.NormalEstimator(K, 3072, 4096)
+    n, m = est(d)
+    rn, rm = est(torch.roll(d, 1, dims=0).contiguous())
+    ms = _time(lambda: nrm.angle_mse(est, n, m, rn, rm), reps)
+    px = 4096 * 3072
+    return ms, px, px * 34
+
+
 def case_multiscale(form: str, reps: int):
     d, K = scenes.random_frame(4999, 4096, 3072, "cuda", kind="f32", holes=False, clip_range=False)
     est = nrm.NormalEstimator(K, 3072, 4096)
@@ -116,7 +136,7 @@ def case_multiscale_batch(form: str, frames: int, reps: int):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["forward", "adjoint", "adjoint_batch", "plane_fit", "multiscale",
-                                     "multiscale_batch"])
+                                     "multiscale_batch", "spherical", "angle_mse"])
     ap.add_argument("--radius", type=int, default=2)
     ap.add_argument("--form", choices=["pair", "quad"], default="pair")
     ap.add_argument("--reps", type=int, default=20)
@@ -131,6 +151,10 @@ def main(argv=None):
         ms, px, nbytes = case_plane_fit(a.radius, a.reps)
     elif a.case == "multiscale":
         ms, px, nbytes = case_multiscale(a.form, a.reps)
+    elif a.case == "spherical":
+        ms, px, nbytes = case_spherical(a.reps)
+    elif a.case == "angle_mse":
+        ms, px, nbytes = case_angle_mse(a.reps)
     elif a.case == "multiscale_batch":
         ms, px, nbytes = case_multiscale_batch(a.form, a.frames or 8, a.reps)
     else:
