@@ -17,6 +17,7 @@ machine without the built library or a GPU every call raises.
 from __future__ import annotations
 
 import ctypes
+from collections import OrderedDict
 from dataclasses import dataclass, field
 from typing import Sequence
 
@@ -571,7 +572,23 @@ def angle_mse(est, normals, valid, ref_normals, ref_valid, stream=None) -> torch
     return out
 
 
-_batch_estimators: dict = {}
+# Handles made by the functional calls below, most recently used last; at most
+# _CACHE_MAX per cache (an evicted handle is released once nothing refers to
+# it, e.g. after the backward pass of a graph that saved it).
+_CACHE_MAX = 32
+_batch_estimators: "OrderedDict" = OrderedDict()
+
+
+def _cached(cache: "OrderedDict", key, make):
+    est = cache.get(key)
+    if est is None:
+        est = make()
+        cache[key] = est
+        while len(cache) > _CACHE_MAX:
+            cache.popitem(last=False)
+    else:
+        cache.move_to_end(key)
+    return est
 
 
 def estimate_normals_batch(depth: torch.Tensor, K, params: NormalParams | None = None):
@@ -582,15 +599,15 @@ def estimate_normals_batch(depth: torch.Tensor, K, params: NormalParams | None =
     Ks = tuple(tuple(float(v) for v in k) for k in K) if len(K) == B and hasattr(K[0], "__len__") \
         else tuple(tuple(float(v) for v in K) for _ in range(B))
     key = (repr(params), depth.device.index)
-    est = _batch_estimators.get(key)
-    if est is None:
+
+    def make():
         with torch.cuda.device(depth.device):
-            est = BatchedEstimator(params, device=depth.device)
-        _batch_estimators[key] = est
-    return NormalsBatchFunction.apply(depth, Ks, est)
+            return BatchedEstimator(params, device=depth.device)
+
+    return NormalsBatchFunction.apply(depth, Ks, _cached(_batch_estimators, key, make))
 
 
-_estimators: dict = {}
+_estimators: "OrderedDict" = OrderedDict()
 
 
 def estimate_normals(depth: torch.Tensor, K, params: NormalParams | None = None):
@@ -598,10 +615,10 @@ def estimate_normals(depth: torch.Tensor, K, params: NormalParams | None = None)
     Handles are cached per (shape, K, params, device)."""
     params = params or NormalParams()
     key = (tuple(depth.shape), tuple(float(v) for v in K), repr(params), depth.device.index)
-    est = _estimators.get(key)
-    if est is None:
+
+    def make():
         with torch.cuda.device(depth.device):
-            est = NormalEstimator(K, depth.shape[0], depth.shape[1], params,
-                                  in_dtype="f32" if depth.dtype == torch.float32 else "u16")
-        _estimators[key] = est
-    return NormalsFunction.apply(depth, est)
+            return NormalEstimator(K, depth.shape[0], depth.shape[1], params,
+                                   in_dtype="f32" if depth.dtype == torch.float32 else "u16")
+
+    return NormalsFunction.apply(depth, _cached(_estimators, key, make))

@@ -156,3 +156,19 @@ def test_binding_refuses_tensors_the_library_cannot_write():
         nrm._check_dense(torch.empty((2, 3)), (2, 3), torch.float32, dev, "x")
     with pytest.raises(ValueError, match="CUDA tensor"):
         nrm._check_cuda(torch.empty((2, 3), dtype=torch.uint8), "mask", dev)
+
+
+def test_functional_handle_cache_is_bounded():
+    """The handles the functional calls create are kept most-recently-used
+    last and at most _CACHE_MAX of them."""
+    from collections import OrderedDict
+
+    import paper_2209_08241_gb300 as nrm
+
+    cache = OrderedDict()
+    made = []
+    for i in range(nrm._CACHE_MAX + 5):
+        nrm._cached(cache, i, lambda i=i: made.append(i) or f"h{i}")
+    assert len(cache) == nrm._CACHE_MAX and list(cache)[0] == 5
+    assert nrm._cached(cache, 5, lambda: "new") == "h5" and list(cache)[-1] == 5
+    assert len(made) == nrm._CACHE_MAX + 5
