@@ -123,8 +123,8 @@ class _Handle:
         self.params = params
         self.in_dtype = in_dtype
         self.H, self.W = int(H), int(W)
-        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
-                                   else torch.device(device).index or 0)
+        index = None if device is None else torch.device(device).index
+        self.device = torch.device("cuda", torch.cuda.current_device() if index is None else index)
         h = ctypes.c_void_p()
         c_params = params.to_c(in_dtype)
         with torch.cuda.device(self.device):
