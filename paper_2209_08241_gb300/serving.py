@@ -31,7 +31,13 @@ from typing import Callable, Optional
 
 import torch
 
-from . import BatchedEstimator, NormalEstimator, NormalParams, _lib
+from . import BatchedEstimator, NormalEstimator, NormalParams, _cached, _lib
+
+
+def _device(device) -> torch.device:
+    """The CUDA device a server runs on: ``device``, else the current one."""
+    index = None if device is None else torch.device(device).index
+    return torch.device("cuda", torch.cuda.current_device() if index is None else index)
 
 
 @dataclass
@@ -131,8 +137,7 @@ class NormalServer:
                  streams: int = 3, max_batch: int = 256, device=None,
                  on_done: Callable[[Request], None] | None = None):
         self.params = params or NormalParams()
-        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
-                                   else torch.device(device).index or 0)
+        self.device = _device(device)
         self.pool = BufferPool(budget_bytes, self.params.torch_out_dtype, self.device)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(streams)]
         self.handles = [BatchedEstimator(self.params, device=self.device) for _ in range(streams)]
@@ -226,11 +231,10 @@ class PlainServer:
     def __init__(self, params: NormalParams | None = None, budget_bytes: int = 40 << 30, device=None,
                  on_done: Callable[[Request], None] | None = None):
         self.params = params or NormalParams()
-        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
-                                   else torch.device(device).index or 0)
+        self.device = _device(device)
         self.pool = BufferPool(budget_bytes, self.params.torch_out_dtype, self.device)
         self.stream = torch.cuda.Stream(self.device)
-        self.estimators: dict = {}
+        self.estimators: collections.OrderedDict = collections.OrderedDict()
         self.waiting: collections.deque = collections.deque()
         self.inflight: collections.deque = collections.deque()
         self.on_done = on_done
@@ -245,13 +249,10 @@ class PlainServer:
     def _estimator(self, r: Request) -> NormalEstimator:
         H, W = r.depth.shape
         key = (H, W, r.depth.dtype, tuple(r.K))
-        est = self.estimators.get(key)
-        if est is None:
-            est = NormalEstimator(r.K, H, W, self.params,
-                                  in_dtype="u16" if r.depth.dtype == torch.uint16 else "f32",
-                                  device=self.device)
-            self.estimators[key] = est
-        return est
+        return _cached(self.estimators, key,
+                       lambda: NormalEstimator(r.K, H, W, self.params,
+                                               in_dtype="u16" if r.depth.dtype == torch.uint16 else "f32",
+                                               device=self.device))
 
     def poll(self):
         now = None
