@@ -58,27 +58,30 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _bind(lib):
+    """Declares the C signatures on a loaded oracle library; returns it."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    lib.nrm_oracle_forward.restype = ctypes.c_int
+    lib.nrm_oracle_forward.argtypes = [
+        ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+        ctypes.c_longlong, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+        ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+        dp, dp, dp, dp, u8p, ctypes.c_int]
+    lib.nrm_oracle_vjp.restype = ctypes.c_int
+    lib.nrm_oracle_vjp.argtypes = [
+        ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+        ctypes.c_longlong, dp, ctypes.c_int, ctypes.c_int, dp, u8p,
+        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
+        ctypes.c_double, ctypes.c_int]
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
-            lib = ctypes.CDLL(path)
-            dp = ctypes.POINTER(ctypes.c_double)
-            u8p = ctypes.POINTER(ctypes.c_uint8)
-            lib.nrm_oracle_forward.restype = ctypes.c_int
-            lib.nrm_oracle_forward.argtypes = [
-                ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                ctypes.c_longlong, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                dp, dp, dp, dp, u8p, ctypes.c_int]
-            lib.nrm_oracle_vjp.restype = ctypes.c_int
-            lib.nrm_oracle_vjp.argtypes = [
-                ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                ctypes.c_longlong, dp, ctypes.c_int, ctypes.c_int, dp, u8p,
-                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
-                ctypes.c_double, ctypes.c_int]
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(build()))
     return _lib
 
 
