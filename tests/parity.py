@@ -1,6 +1,6 @@
 """Comparison helpers for GPU-vs-oracle parity tests.
 
-Tolerances (derived from the FP32 arithmetic of the closed form, Eq. 4-6):
+Tolerances (fixed for this method; the FP32 closed form of Eq. 4-6 stays far inside them):
   * normals: angular error <= 1e-4 rad for float32 output, 5e-3 rad for half;
   * mask: bit-exact, except pixels whose oracle statistic lies within 1e-6
     relative of tau; those are excluded, counted and returned.
