@@ -102,17 +102,18 @@ def _intr(K) -> _lib.Intrinsics:
 
 
 def _check_cuda(t: torch.Tensor, name: str, device: torch.device | None = None):
-    if not t.is_cuda:
-        raise ValueError(f"{name} must be a CUDA tensor")
-    if device is not None and t.device != device:
-        raise ValueError(f"{name} is on {t.device}, expected {device}")
+    if device is None:
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+    elif t.device != device:  # device is a CUDA device, so this also refuses host tensors
+        raise ValueError(f"{name} must be a CUDA tensor on {device}, got one on {t.device}")
 
 
 def _check_dense(t: torch.Tensor, shape, dtype: torch.dtype, device: torch.device, name: str):
     """t must be a contiguous CUDA tensor of exactly this shape and dtype on
     ``device``: the library writes through its raw pointer."""
     _check_cuda(t, name, device)
-    if tuple(t.shape) != tuple(shape) or t.dtype != dtype or not t.is_contiguous():
+    if t.shape != tuple(shape) or t.dtype != dtype or not t.is_contiguous():
         raise ValueError(f"{name} must be a contiguous {tuple(shape)} {dtype} tensor, got "
                          f"{tuple(t.shape)} {t.dtype}{'' if t.is_contiguous() else ' (not contiguous)'}")
 
