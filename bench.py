@@ -889,10 +889,12 @@ def main(argv=None):
                     help="frames per GPU (default 64; smaller only for profiling)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--config", default="", help="tile_x,tile_y,threads,stages[,ctas_per_sm] (skips the autotuner)")
-    ap.add_argument("--skip-extra", action="store_true")
-    ap.add_argument("--skip-e2e", action="store_true")
-    ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--skip-serving", action="store_true")
+    # The --skip-* switches leave out whole secondary measurements (for short
+    # profiling runs); the timed headline step is the same with or without them.
+    ap.add_argument("--skip-extra", action="store_true", help="omit the extra kernel measurements")
+    ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end host-buffer measurement")
+    ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
+    ap.add_argument("--skip-serving", action="store_true", help="omit the serving sweep")
     ap.add_argument("--serving-full", action="store_true",
                     help="serving sweep at 1..8000 frames/s, 60 s each (default: 100..8000, 2 s each)")
     args = ap.parse_args(argv)
