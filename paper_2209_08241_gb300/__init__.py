@@ -46,6 +46,7 @@ class NormalParams:
     orient_to_camera: bool = False
 
     def to_c(self, in_dtype: int) -> _lib.Params:
+        """The C ``nrm_params`` struct for these parameters and an input dtype."""
         p = _lib.Params()
         p.alpha = int(self.alpha)
         p.mask_mode = {"secant": NRM_MASK_SECANT, "raw": NRM_MASK_RAW}[self.mask_mode]
@@ -80,6 +81,7 @@ def decode_oct16(codes: torch.Tensor) -> torch.Tensor:
 
 
 def version() -> str:
+    """The library's version string (with the architecture it was built for)."""
     return _lib.load().nrm_version().decode()
 
 
@@ -182,6 +184,7 @@ class NormalEstimator(_Handle):
         self.K = tuple(float(v) for v in K)
 
     def new_outputs(self):
+        """A new (normals, valid) pair of this estimator's size and output dtype."""
         n = torch.empty((self.H, self.W, self.params.out_channels), dtype=self.params.torch_out_dtype,
                         device=self.device)
         m = torch.empty((self.H, self.W), dtype=torch.uint8, device=self.device)
@@ -356,6 +359,7 @@ class BatchedEstimator(_Handle):
         return arr, outs
 
     def run(self, frames_array, n: int, stream=None):
+        """One batched launch over the first n frames of a ``make_frames`` array."""
         _lib.check(self.lib.nrm_estimate_batched(self.h, frames_array, int(n), _stream_ptr(stream)),
                    "nrm_estimate_batched")
 
@@ -373,6 +377,7 @@ class BatchedEstimator(_Handle):
 
     def multiscale(self, items: Sequence, alphas=(1, 2, 3, 4), form: str = "pair", outputs: Sequence | None = None,
                    stream=None):
+        """``run_multiscale`` on [(depth, K), ...]; returns the (normals, valid) outputs."""
         arr, outs = self.make_frames(items, outputs)
         self.run_multiscale(arr, len(items), alphas, form, stream)
         return outs
@@ -461,6 +466,7 @@ class BatchedEstimator(_Handle):
         return arr, outs
 
     def run_backward(self, grad_frames_array, n: int, stream=None):
+        """One batched adjoint launch over the first n frames of a ``make_grad_frames`` array."""
         _lib.check(self.lib.nrm_backward_batched(self.h, grad_frames_array, int(n), _stream_ptr(stream)),
                    "nrm_backward_batched")
 
@@ -474,6 +480,9 @@ class BatchedEstimator(_Handle):
 
     def autotune(self, items: Sequence, outputs: Sequence | None = None, cache_path: str | None = None,
                  stream=None) -> dict:
+        """Times the compiled launch geometries (tile shape, pipeline depth,
+        CTAs per SM) on these frames and keeps the fastest (``nrm_autotune``;
+        cached in ``cache_path`` when given); returns the chosen configuration."""
         arr, _ = self.make_frames(items, outputs)
         cp = cache_path.encode() if cache_path else None
         _lib.check(self.lib.nrm_autotune(self.h, arr, len(items), _stream_ptr(stream), cp), "nrm_autotune")

@@ -86,11 +86,13 @@ class BufferPool:
 
     @staticmethod
     def set_bytes(H: int, W: int, depth_dtype: torch.dtype, out_dtype: torch.dtype) -> int:
+        """Device bytes of one buffer set: depth, normals and mask of an H x W frame."""
         eb = 2 if depth_dtype == torch.uint16 else 4
         ob = {torch.float32: 16, torch.float16: 8, torch.int16: 4}[out_dtype]
         return H * W * (eb + ob + 1)
 
     def acquire(self, H: int, W: int, depth_dtype: torch.dtype) -> Optional[BufferSet]:
+        """A free buffer set for this frame size, a new one within the budget, or None."""
         key = (H, W, depth_dtype)
         if self.free[key]:
             b = self.free[key].pop()
@@ -118,6 +120,7 @@ class BufferPool:
         return b
 
     def release(self, b: BufferSet):
+        """Returns a set to the free list (it stays allocated for reuse)."""
         self.in_use -= b.nbytes
         self.free[b.key].append(b)
 
@@ -151,9 +154,11 @@ class NormalServer:
         self._frames = (_lib.Frame * self.max_batch)()
 
     def submit(self, req: Request):
+        """Queues a request; it is admitted and launched by a later poll()."""
         self.waiting.append(req)
 
     def busy(self) -> bool:
+        """True while requests are waiting or on the GPU."""
         return bool(self.waiting or self.inflight)
 
     def _retire(self):
@@ -216,10 +221,12 @@ class NormalServer:
         self._launch()
 
     def drain(self):
+        """Polls until every submitted request has completed."""
         while self.busy():
             self.poll()
 
     def sync_status(self):
+        """Raises the first device-side error any of the server's handles recorded."""
         for h in self.handles:
             h.sync_status()
 
@@ -241,9 +248,11 @@ class PlainServer:
         self.completed = 0
 
     def submit(self, req: Request):
+        """Queues a request; it is admitted and launched by a later poll()."""
         self.waiting.append(req)
 
     def busy(self) -> bool:
+        """True while requests are waiting or on the GPU."""
         return bool(self.waiting or self.inflight)
 
     def _estimator(self, r: Request) -> NormalEstimator:
@@ -255,6 +264,7 @@ class PlainServer:
                                                device=self.device))
 
     def poll(self):
+        """Retire finished requests, then launch waiting ones whose buffers fit."""
         now = None
         while self.inflight and self.inflight[0][0].query():
             ev, r = self.inflight.popleft()
@@ -282,10 +292,12 @@ class PlainServer:
             self.inflight.append((ev, r))
 
     def drain(self):
+        """Polls until every submitted request has completed."""
         while self.busy():
             self.poll()
 
     def sync_status(self):
+        """Raises the first device-side error any of the server's handles recorded."""
         for est in self.estimators.values():
             est.sync_status()
 
@@ -308,6 +320,7 @@ def run_arrivals(server, requests: list, t0: float | None = None):
 
 
 def latency_summary(requests: list, duration: float) -> dict:
+    """Served Mpx/s and p50 / p99 / max latency (ms) of completed requests."""
     lat = sorted(r.latency for r in requests)
     n = len(lat)
     px = sum(r.pixels for r in requests)
