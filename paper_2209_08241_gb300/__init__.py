@@ -617,6 +617,16 @@ def estimate_normals_batch(depth: torch.Tensor, K, params: NormalParams | None =
     return NormalsBatchFunction.apply(depth, Ks, _cached(_batch_estimators, key, make))
 
 
+def estimate(depth: torch.Tensor, K, params: NormalParams | None = None):
+    """Normals and mask of a depth map: ``(H, W)`` -> ((H, W, 4), (H, W)) through
+    ``estimate_normals``, or a stack ``(B, H, W)`` -> ((B, H, W, 4), (B, H, W))
+    through ``estimate_normals_batch`` (K: one for all frames or one per
+    frame). Differentiable with respect to float32 depth, masks held fixed."""
+    if depth.dim() == 3:
+        return estimate_normals_batch(depth, K, params)
+    return estimate_normals(depth, K, params)
+
+
 _estimators: "OrderedDict" = OrderedDict()
 
 

@@ -83,3 +83,16 @@ def test_batched_outputs_are_checked():
     with pytest.raises(ValueError):
         b([(d.cpu(), K)])
     b.sync_status()
+
+
+def test_functional_estimate_single_and_stack():
+    """nrm.estimate: a (H, W) map through the single-frame handle, a (B, H, W)
+    stack through one batched launch; both equal the estimator classes."""
+    d = depth()
+    n, m = nrm.estimate(d, K)
+    ref_n, ref_m = nrm.NormalEstimator(K, H, W)(d)
+    assert torch.equal(n, ref_n) and torch.equal(m, ref_m)
+    stack = torch.stack([d, d.flip(0).contiguous()])
+    ns, ms = nrm.estimate(stack, K)
+    assert ns.shape == (2, H, W, 4) and ms.shape == (2, H, W)
+    assert torch.equal(ns[0], ref_n) and torch.equal(ms[0], ref_m)
