@@ -1,12 +1,15 @@
-"""Property-based pins of the forward oracle over random planes, intrinsics,
-pixel distances and depth maps (Section 3.1, Eq. 4-6; Section 3.2):
+"""Property-based pins of the oracles over random planes, intrinsics, pixel
+distances and depth maps (Section 3.1, Eq. 4-6; Section 3.2; the multi-scale
+average of Section 2; the plane fit of Sections 1 and 4):
 
 * a plane n0 . P = c0 seen from the origin gives n_hat = n0 / |n0| exactly on
   every pixel whose stencil is inside the image;
 * n . (u1, v1, 1) = alpha^2 (d2 + d4)(d3 + d5) / (4 fx fy) for any depths (the
   n_z row of Eq. 6);
 * scaling the depth map by k leaves n_hat and the SECANT statistic unchanged
-  and multiplies the RAW statistic by k^2.
+  and multiplies the RAW statistic by k^2;
+* on a plane, the multi-scale average (either form, any scale set) and the
+  plane fit (any radius) return the plane's normal.
 """
 import numpy as np
 import pytest
@@ -87,3 +90,43 @@ def test_depth_scaling(seed, k, alpha):
     s1 = oracle.forward(D, K, alpha=alpha, stat_mode=oracle.STAT_SECANT, tau=BIG)
     s2 = oracle.forward(k * D, K, alpha=alpha, stat_mode=oracle.STAT_SECANT, tau=BIG)
     np.testing.assert_allclose(s2.stat[v], s1.stat[v], rtol=1e-12)
+
+
+@settings(max_examples=40, deadline=None, derandomize=True)
+@given(nx=st.floats(-0.5, 0.5), ny=st.floats(-0.5, 0.5), c0=st.floats(0.5, 6.0), K=intrinsics,
+       alphas=st.lists(st.integers(1, 4), min_size=1, max_size=4, unique=True),
+       form=st.sampled_from(["pair", "quad"]))
+def test_multiscale_random_plane_is_exact(nx, ny, c0, K, alphas, form):
+    """Every scale's stencil on a plane spans the plane, so the averaged
+    normal is the plane's for any set of pixel distances and either form."""
+    from oracle.multiscale import multiscale
+    H, W = 16, 18
+    n0 = np.array([nx, ny, 1.0])
+    n0 /= np.linalg.norm(n0)
+    along = rays(H, W, K) @ n0
+    assume(along.min() > 0.05)
+    res = multiscale(c0 / along, K, alphas, form, oracle.STAT_RAW, BIG)
+    v = res.valid.astype(bool)
+    amax = max(alphas)
+    lo = 0 if form == "pair" else amax
+    assert v.sum() == (H - amax - lo) * (W - amax - lo)
+    assert np.abs(res.n_hat[v] @ n0 - 1.0).max() < 1e-11
+
+
+@settings(max_examples=30, deadline=None, derandomize=True)
+@given(nx=st.floats(-0.5, 0.5), ny=st.floats(-0.5, 0.5), c0=st.floats(0.5, 6.0), K=intrinsics,
+       radius=st.integers(1, 3))
+def test_plane_fit_random_plane_is_exact(nx, ny, c0, K, radius):
+    """The window of a plane has a zero smallest eigenvalue whose eigenvector
+    is the plane's normal, oriented away from the camera."""
+    from oracle.plane_fit import plane_fit
+    H, W = 14, 15
+    n0 = np.array([nx, ny, 1.0])
+    n0 /= np.linalg.norm(n0)
+    along = rays(H, W, K) @ n0
+    assume(along.min() > 0.05)
+    n, valid, ev = plane_fit(c0 / along, K, radius)
+    v = valid.astype(bool)
+    assert v.sum() == (H - 2 * radius) * (W - 2 * radius)
+    assert np.abs(n[v] @ n0 - 1.0).max() < 1e-9
+    assert (ev[v][:, 0] <= 1e-12 * ev[v][:, 2]).all()
