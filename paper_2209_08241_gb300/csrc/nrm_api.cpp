@@ -165,6 +165,8 @@ int make_desc(FrameDesc* d, const void* depth, void* normals, uint8_t* valid, in
   d->points = points;
   d->point_scale = (float)s;
   d->mask_align = valid ? std::min(pow2_align((uintptr_t)valid, 16), pow2_align((uintptr_t)out_pitch, 16)) : 1;
+  const long long bpp = p.out_dtype == NRM_OUT_F32X4 ? 16 : (p.out_dtype == NRM_OUT_F16X4 ? 8 : 4);
+  d->out_align = normals ? std::min(pow2_align((uintptr_t)normals, 16), pow2_align((uintptr_t)(out_pitch * bpp), 16)) : 1;
   const int eb = in_dtype == NRM_IN_U16_MM ? 2 : 4;
   const bool aligned = ((uintptr_t)depth % 16 == 0) && ((depth_pitch * eb) % 16 == 0) &&
                        (depth_pitch * eb) < (1LL << 40) && H > 0 && W > 0;

@@ -199,6 +199,7 @@ struct TileFrame {
   float inv_fx, inv_fy, cx, cy;
   int H, W;
   int mask_align;
+  int out_align;
   int in_dtype;
   long long out_pitch;
   void* normals;
@@ -221,6 +222,7 @@ __device__ __forceinline__ TileFrame tile_frame(const FrameDesc& fd, float sign)
   f.H = fd.H;
   f.W = fd.W;
   f.mask_align = fd.mask_align;
+  f.out_align = fd.out_align;
   f.in_dtype = fd.in_dtype;
   f.out_pitch = fd.out_pitch;
   f.normals = fd.normals;
@@ -317,35 +319,28 @@ __device__ __forceinline__ float rcp_ftz(float x) {
   return y;
 }
 
-// Round to the nearest integer (ties to even) for |x| < 2^22: adding 1.5 * 2^23
-// leaves the integer in the low mantissa bits.
-__device__ __forceinline__ int round_small(float x) {
-  return __float_as_int(x + 12582912.0f) - 0x4B400000;
+// Octahedral code of the direction of a normal (Meyer et al. 2010; Cigolle et
+// al. 2014): p = (n_x, n_y) / (|n_x| + |n_y| + |n_z|); where n_z < 0 the lower
+// half is folded over the diagonals, p <- (1 - |p_y|, 1 - |p_x|) with the signs of
+// p. Since 1 - |p_y| = (|n_x| + |n_z|) / l1, both cases are
+// p = (n_x + sgn(n_x) m, n_y + sgn(n_y) m) / l1 with m = max(-n_z, 0). Each
+// coordinate becomes the signed 16-bit integer round(32767 p) (|32767 p| <=
+// 32767 up to rounding, far below 32767.5, so it fits): one fused multiply-add
+// with 1.5 * 2^23 rounds to the nearest integer, which then sits in the low
+// mantissa bits (two's complement modulo 2^16). x in the low half of the
+// word, y in the high half. The code does not depend on the length of n.
+__device__ __forceinline__ uint32_t oct16_code(float nx, float ny, float nz) {
+  const float s = 32767.0f * rcp_ftz(fabsf(nx) + fabsf(ny) + fabsf(nz));
+  const float m = fmaxf(-nz, 0.0f);
+  const float tx = nx + copysignf(m, nx);
+  const float ty = ny + copysignf(m, ny);
+  const float kRound = 12582912.0f;  // 1.5 * 2^23
+  return __byte_perm(__float_as_uint(fmaf(tx, s, kRound)), __float_as_uint(fmaf(ty, s, kRound)), 0x5410);
 }
 
-// Octahedral codes of the directions of two normals (Meyer et al. 2010; Cigolle
-// et al. 2014): p = (n_x, n_y) / (|n_x| + |n_y| + |n_z|); where n_z < 0 the lower
-// half is folded over the diagonals, p <- (1 - |p_y|, 1 - |p_x|) with the signs of
-// p. Each coordinate, in [-1, 1] up to rounding, becomes the signed 16-bit integer
-// round(32767 p) (|32767 p| < 32767.5, so it fits); x in the low half of the word,
-// y in the high half. The code does not depend on the length of n.
 __device__ __forceinline__ void oct16_encode2(float2 nx, float2 ny, float2 nz, uint32_t& ca, uint32_t& cb) {
-  const float2 ax = f2(fabsf(nx.x), fabsf(nx.y)), ay = f2(fabsf(ny.x), fabsf(ny.y));
-  const float2 l1 = __fadd2_rn(__fadd2_rn(ax, ay), f2(fabsf(nz.x), fabsf(nz.y)));
-  const float2 r = f2(rcp_ftz(l1.x), rcp_ftz(l1.y));
-  const float2 px = __fmul2_rn(nx, r), py = __fmul2_rn(ny, r);
-  const float2 one = f2(1.0f, 1.0f);
-  const float2 m1 = f2(-1.0f, -1.0f);
-  const float2 rx = __ffma2_rn(m1, f2(fabsf(py.x), fabsf(py.y)), one);  // 1 - |p_y|
-  const float2 ry = __ffma2_rn(m1, f2(fabsf(px.x), fabsf(px.y)), one);  // 1 - |p_x|
-  const float qxa = nz.x < 0.0f ? copysignf(rx.x, px.x) : px.x;
-  const float qya = nz.x < 0.0f ? copysignf(ry.x, py.x) : py.x;
-  const float qxb = nz.y < 0.0f ? copysignf(rx.y, px.y) : px.y;
-  const float qyb = nz.y < 0.0f ? copysignf(ry.y, py.y) : py.y;
-  const float2 s = f2(32767.0f, 32767.0f);
-  const float2 ua = __fmul2_rn(f2(qxa, qya), s), ub = __fmul2_rn(f2(qxb, qyb), s);
-  ca = ((uint32_t)round_small(ua.x) & 0xFFFFu) | ((uint32_t)round_small(ua.y) << 16);
-  cb = ((uint32_t)round_small(ub.x) & 0xFFFFu) | ((uint32_t)round_small(ub.y) << 16);
+  ca = oct16_code(nx.x, ny.x, nz.x);
+  cb = oct16_code(nx.y, ny.y, nz.y);
 }
 
 // Expands the low 2 or 4 bits of b into bytes of value 0/1.

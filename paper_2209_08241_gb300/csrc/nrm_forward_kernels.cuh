@@ -21,7 +21,7 @@
 //                         synchronising only among themselves (named barrier 1).
 #pragma once
 
-#include "nrm_device.cuh"
+#include "nrm_forward_vec.cuh"
 
 // The compiled tile configurations (tile_x, tile_y, compute threads); the
 // first is the default. TX is at most 128 so that the halo box (TX + 2 pad <=
@@ -44,6 +44,7 @@ static_assert(sizeof(StageInfo) <= kStageInfoBytes, "StageInfo must fit its slot
 template <int TX, int TY, int NT, int OUT, bool POINTS>
 __global__ void __launch_bounds__(NT)
     fwd_plain_kernel(const __grid_constant__ FrameDesc fd, const Globals g) {
+  static_assert(TX / 2 + TY <= NT, "one thread per table entry");
   extern __shared__ __align__(128) unsigned char smem[];
   const int alpha = g.alpha;
   const bool u16 = fd.in_dtype == NRM_IN_U16_MM;
@@ -59,9 +60,12 @@ __global__ void __launch_bounds__(NT)
   float* F = reinterpret_cast<float*>(smem + SB);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SB + ftile_bytes_for(TX, TY, alpha));
   const TileFrame tf = tile_frame(fd, g.sign);
-
+  // The column and row tables do not depend on the depth; the barrier at the
+  // end of the staging publishes them with the decoded tile.
+  fill_tile_tables<TX, TY>(reinterpret_cast<float4*>(smem + SB + ftile_float_bytes(TX, TY, alpha)), tf, gx0, gy0,
+                           threadIdx.x);
   if (!stage_plain_tile<NT>(smem, F, bar, fd, tf, alpha, padx, bw, bh, pad4, fw, gx0, gy0, g)) return;
-  compute_tile_any<TX, TY, NT, OUT, POINTS>(F, fw, pad4, tf, gx0, gy0, g);
+  compute_tile_fwd<TX, TY, NT, OUT, POINTS>(F, fw, pad4, tf, gx0, gy0, g);
 }
 
 // A work-list index: through the read-only data path from global memory, or a
@@ -79,6 +83,7 @@ __device__ __forceinline__ int load_index(const int* p) {
 // kernel-parameter space.
 template <int TX, int TY, int NT, class Compute, bool FENCE = true>
 __device__ __forceinline__ void persistent_pipeline(const BatchArgs& args, const Globals& g, const Compute& compute) {
+  static_assert(TX / 2 + TY <= NT, "one thread per table entry");
   extern __shared__ __align__(128) unsigned char smem[];
   const int S = args.stages;
   const unsigned SB = args.stage_bytes;
@@ -166,17 +171,16 @@ __device__ __forceinline__ void persistent_pipeline(const BatchArgs& args, const
     float* F = reinterpret_cast<float*>(fbase + (i & 1) * FB);
     if (ok) {
       if (si.tma) {
-        const unsigned char* stage = smem + (size_t)s * SB;
-        if (u16)
-          decode_tile<NT>(reinterpret_cast<const uint16_t*>(stage), F, fw, bh, bw, padx - pad4);
-        else
-          decode_tile<NT>(reinterpret_cast<const float*>(stage), F, fw, bh, bw, 0);
+        decode_staged<TX, TY, NT>(smem + (size_t)s * SB, F, u16, alpha, fw, bh, bw, padx - pad4);
       } else {
         if (u16)
           load_tile_decoded<uint16_t, NT>(F, fw, bh, si.f, gx0 - pad4, gy0 - alpha);
         else
           load_tile_decoded<float, NT>(F, fw, bh, si.f, gx0 - pad4, gy0 - alpha);
       }
+      fill_tile_tables<TX, TY>(reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(F) +
+                                                         ftile_float_bytes(TX, TY, alpha)),
+                               si.f, gx0, gy0, threadIdx.x);
     }
     if (bar_red_or(1, NT, !ok)) {
       if (threadIdx.x == 0) record_error(g.status, NRM_ERR_TIMEOUT);
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(NT + 32)
   args.tile_begin = pb.tile_begin;
   args.frames = pb.frames;
   auto compute = [&](const float* F, int fw, int pad4, const TileFrame& tf, int gx0, int gy0) {
-    compute_tile_any<TX, TY, NT, OUT, false>(F, fw, pad4, tf, gx0, gy0, g);
+    compute_tile_fwd<TX, TY, NT, OUT, false>(F, fw, pad4, tf, gx0, gy0, g);
   };
   persistent_pipeline<TX, TY, NT, decltype(compute), false>(args, g, compute);
 }
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(NT + 32)
     fwd_persistent_kernel(const BatchArgs args, const Globals g) {
   persistent_pipeline<TX, TY, NT>(args, g,
                                   [&](const float* F, int fw, int pad4, const TileFrame& tf, int gx0, int gy0) {
-                                    compute_tile_any<TX, TY, NT, OUT, POINTS>(F, fw, pad4, tf, gx0, gy0, g);
+                                    compute_tile_fwd<TX, TY, NT, OUT, POINTS>(F, fw, pad4, tf, gx0, gy0, g);
                                   });
 }
 

@@ -44,6 +44,7 @@ struct alignas(128) FrameDesc {
   int use_tma;             // 1: TMA tile loads; 0: plain loads (unaligned base or pitch)
   int mask_align;          // bytes: largest power of two (<= 16) dividing mask base and pitch
   float point_scale;       // metres per decoded depth unit (u16: depth_scale; f32: 1)
+  int out_align;           // bytes: largest power of two (<= 16) dividing normals base and row pitch in bytes
   float* points;           // optional organised point cloud (x, y, z, 0) per pixel, pitch out_pitch; or NULL
 };
 static_assert(sizeof(FrameDesc) == 256, "FrameDesc layout");
@@ -116,9 +117,15 @@ NRM_HD inline unsigned stage_bytes_for(int tile_x, int tile_y, int alpha, int eb
 }
 // Bytes of the decoded float halo tile: (TX + 2 pad_x(alpha, 4)) x (TY + 2 alpha)
 // floats for either input dtype.
-NRM_HD inline unsigned ftile_bytes_for(int tile_x, int tile_y, int alpha) {
+NRM_HD inline unsigned ftile_float_bytes(int tile_x, int tile_y, int alpha) {
   unsigned b = (unsigned)((tile_x + 2 * pad_x(alpha, 4)) * (tile_y + 2 * alpha) * 4);
   return (b + 127) / 128 * 128;
+}
+// Bytes of a decoded tile's buffer: the float tile, then its column and row
+// tables (one float4 per column pair and per row).
+NRM_HD inline unsigned ftile_bytes_for(int tile_x, int tile_y, int alpha) {
+  unsigned t = (unsigned)((tile_x / 2 + tile_y) * 16);
+  return ftile_float_bytes(tile_x, tile_y, alpha) + (t + 127) / 128 * 128;
 }
 // Dynamic shared memory of the plain kernel: staging buffer, decoded tile,
 // barrier.
