@@ -11,8 +11,14 @@
 // allocates device memory.
 //
 // The host needs the device address of the array: in host code the array's
-// name is only a host-side stand-in. It is looked up once per device with
-// cudaGetSymbolAddress, with that device current, on the first call made on it.
+// name is only a host-side stand-in. It is looked up with cudaGetSymbolAddress,
+// with the device current, on every call (a cheap runtime query): the first
+// call on a device, and the first call after the device's context was reset
+// (the address may then differ), also set the kernels' shared-memory limit.
+//
+// A call refuses a stream that is being captured: it copies the descriptors
+// from a host array that the next call overwrites, so a captured copy would
+// replay whatever the latest call left there.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -49,10 +55,10 @@ DeviceState g_devices[kMaxDevices];
 alignas(256) unsigned char g_host_block[kScratchBytes];  // host image of the block
 
 int setup_device(int device, DeviceState& st) {
-  if (st.ready) return NRM_OK;
   void* ptr = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
   if (e != cudaSuccess) return nrm::host_fail(NRM_ERR_CUDA, cudaGetErrorString(e));
+  if (st.ready && st.scratch == ptr) return NRM_OK;
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) return nrm::host_fail(NRM_ERR_CUDA, cudaGetErrorString(e));
@@ -72,6 +78,7 @@ int setup_device(int device, DeviceState& st) {
 
 extern "C" int nrm_estimate_batched_noalloc(const nrm_frame* frames, int n, const nrm_params* params,
                                             int* device_status, void* cuda_stream) {
+  nrm::host_clear_error();
   if (n < 0) return nrm::host_fail(NRM_ERR_INVALID_ARG, "n < 0");
   if (n == 0) return NRM_OK;
   if (!frames) return nrm::host_fail(NRM_ERR_INVALID_ARG, "frames is NULL");
@@ -94,8 +101,17 @@ extern "C" int nrm_estimate_batched_noalloc(const nrm_frame* frames, int n, cons
   if (total == 0) return NRM_OK;
   if (total >= (1LL << 31) - 1) return nrm::host_fail(NRM_ERR_UNSUPPORTED, "batch exceeds 2^31 tiles");
 
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(stream, &capture);
+  if (e != cudaSuccess) return nrm::host_fail(NRM_ERR_CUDA, cudaGetErrorString(e));
+  if (capture != cudaStreamCaptureStatusNone)
+    return nrm::host_fail(NRM_ERR_UNSUPPORTED,
+                          "nrm_estimate_batched_noalloc cannot be recorded by stream capture (its descriptor "
+                          "copy reads a host array that later calls overwrite)");
+
   int device = 0;
-  cudaError_t e = cudaGetDevice(&device);
+  e = cudaGetDevice(&device);
   if (e != cudaSuccess) return nrm::host_fail(NRM_ERR_NO_DEVICE, cudaGetErrorString(e));
   if (device < 0 || device >= kMaxDevices) return nrm::host_fail(NRM_ERR_UNSUPPORTED, "device index too large");
 
@@ -122,7 +138,6 @@ extern "C" int nrm_estimate_batched_noalloc(const nrm_frame* frames, int n, cons
   hdr->n_frames = n;
   hdr->total_tiles = acc;
 
-  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   const size_t used = foff + sizeof(nrm::FrameDesc) * (size_t)n;
   e = cudaMemcpyAsync(st.scratch, g_host_block, used, cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) return nrm::host_fail(NRM_ERR_CUDA, cudaGetErrorString(e));
