@@ -324,9 +324,12 @@ NRM_API int nrm_set_config(nrm_handle* h, const nrm_tile_config* cfg);
 
 /* Times every supported configuration on the given batch (which must stay
  * valid during the call; outputs are overwritten), keeps the fastest in the
- * handle and records it in the JSON cache file cache_path (NULL = no file),
- * keyed by GPU name, SM count, frame-size class, dtypes and alpha. If the
- * cache already holds the key, loads it without timing. Synchronous. */
+ * handle and records it in the JSON cache file cache_path, keyed by GPU name,
+ * SM count, frame-size class, dtypes and alpha. cache_path = NULL takes the
+ * process-wide cache file (nrm_set_autotune_cache), if any. If the cache
+ * already holds the key, loads it without timing. The tuned configuration is
+ * also recorded under the handle's own key (nrm_autotune_key), which
+ * nrm_create looks up. Synchronous. */
 NRM_API int nrm_autotune(nrm_handle* h, const nrm_frame* frames, int n, void* cuda_stream,
                  const char* cache_path);
 
@@ -341,6 +344,26 @@ typedef struct {
 NRM_API int nrm_enable_timing(nrm_handle* h, int enable);
 NRM_API int nrm_get_stats(nrm_handle* h, nrm_stats* out); /* waits for pending launches */
 NRM_API int nrm_reset_stats(nrm_handle* h);
+
+/* Autotune cache: a JSON object mapping keys to [tile_x, tile_y, threads,
+ * stages, ctas_per_sm]. These calls need no GPU.
+ *
+ * nrm_set_autotune_cache sets the process-wide cache file (path = NULL clears
+ * it; without a call, the environment variable NRM_AUTOTUNE_CACHE names it).
+ * With a cache file set, nrm_create configures a new handle from the entry of
+ * its key, if there is one, instead of the default geometry, so a process
+ * that tuned a workload once lets later processes skip the sweep.
+ * nrm_autotune_key writes a handle's key (GPU name, SM count, input and output
+ * dtypes, alpha, H x W of the handle) to buf (NUL-terminated; NRM_ERR_INVALID_ARG
+ * if it does not fit in len bytes). nrm_autotune_cache_get reads the entry of
+ * key from the file at path (NRM_ERR_INVALID_ARG if the file or the key is
+ * absent or malformed); nrm_autotune_cache_put adds or replaces it (written to
+ * a temporary file and renamed over path; NRM_ERR_INVALID_ARG if it cannot be
+ * written or key contains a quote or a backslash). */
+NRM_API int nrm_set_autotune_cache(const char* path);
+NRM_API int nrm_autotune_key(const nrm_handle* h, char* buf, int len);
+NRM_API int nrm_autotune_cache_get(const char* path, const char* key, nrm_tile_config* cfg);
+NRM_API int nrm_autotune_cache_put(const char* path, const char* key, const nrm_tile_config* cfg);
 
 /* Largest number of frames nrm_estimate_batched_noalloc accepts per call. */
 #define NRM_NOALLOC_MAX_FRAMES 256
@@ -375,14 +398,19 @@ NRM_API int nrm_reset_stats(nrm_handle* h);
  * descriptors goes through cudaMemcpyAsync from pageable memory, which returns
  * once the source has been read.
  *
- * The first call on a device does a one-time set-up with that device current:
- * it looks up the array's device address (cudaGetSymbolAddress) and sets the
- * kernel's shared-memory limit. Make that first call before any stream capture
- * begins.
+ * Every call looks up the array's device address (cudaGetSymbolAddress) with
+ * the current device; the first call on a device, and the first call after
+ * that device's context was reset (cudaDeviceReset), also set the kernel's
+ * shared-memory limit.
  *
- * Errors: NRM_ERR_UNSUPPORTED for n > NRM_NOALLOC_MAX_FRAMES or a frame with
- * a point-cloud buffer (this entry point writes normals and masks only;
- * nothing is launched); otherwise as nrm_estimate_batched. */
+ * Stream capture: not supported. The descriptor copy reads a host array that
+ * the next call overwrites, so a captured copy would replay stale descriptors;
+ * a call on a stream that is being captured returns NRM_ERR_UNSUPPORTED and
+ * records nothing (the capture stays valid).
+ *
+ * Errors: NRM_ERR_UNSUPPORTED for n > NRM_NOALLOC_MAX_FRAMES, a frame with a
+ * point-cloud buffer (this entry point writes normals and masks only) or a
+ * capturing stream, with nothing launched; otherwise as nrm_estimate_batched. */
 NRM_API int nrm_estimate_batched_noalloc(const nrm_frame* frames, int n, const nrm_params* p,
                                          int* device_status, void* cuda_stream);
 

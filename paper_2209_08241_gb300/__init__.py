@@ -85,6 +85,31 @@ def version() -> str:
     return _lib.load().nrm_version().decode()
 
 
+def set_autotune_cache(path: str | None) -> None:
+    """Sets the process-wide autotune cache file (``nrm_set_autotune_cache``):
+    handles created afterwards start from the tuned geometry recorded for their
+    key, and ``autotune`` without a path reads and records there. None clears it."""
+    _lib.check(_lib.load().nrm_set_autotune_cache(path.encode() if path else None), "nrm_set_autotune_cache")
+
+
+def autotune_cache_get(path: str, key: str) -> dict | None:
+    """The configuration recorded for ``key`` in the cache file, or None."""
+    c = _lib.TileConfig()
+    lib = _lib.load()
+    if lib.nrm_autotune_cache_get(path.encode(), key.encode(), ctypes.byref(c)) != _lib.NRM_OK:
+        return None
+    return {"tile_x": c.tile_x, "tile_y": c.tile_y, "threads": c.threads, "stages": c.stages,
+            "ctas_per_sm": c.ctas_per_sm}
+
+
+def autotune_cache_put(path: str, key: str, tile_x: int, tile_y: int, threads: int, stages: int,
+                       ctas_per_sm: int = 0) -> None:
+    """Adds or replaces the entry of ``key`` in the cache file."""
+    c = _lib.TileConfig(tile_x, tile_y, threads, stages, ctas_per_sm)
+    _lib.check(_lib.load().nrm_autotune_cache_put(path.encode(), key.encode(), ctypes.byref(c)),
+               "nrm_autotune_cache_put")
+
+
 def _in_dtype(t: torch.Tensor) -> int:
     if t.dtype == torch.float32:
         return NRM_IN_F32_M
@@ -152,6 +177,12 @@ class _Handle:
         c = _lib.TileConfig()
         _lib.check(self.lib.nrm_get_config(self.h, ctypes.byref(c)), "nrm_get_config")
         return {k: getattr(c, k) for k, _ in c._fields_}
+
+    def autotune_key(self) -> str:
+        """This handle's key in the autotune cache (``nrm_autotune_key``)."""
+        buf = ctypes.create_string_buffer(512)
+        _lib.check(self.lib.nrm_autotune_key(self.h, buf, len(buf)), "nrm_autotune_key")
+        return buf.value.decode()
 
     def set_config(self, tile_x=128, tile_y=16, threads=256, stages=3, ctas_per_sm=0):
         c = _lib.TileConfig(tile_x, tile_y, threads, stages, ctas_per_sm)
@@ -482,7 +513,8 @@ class BatchedEstimator(_Handle):
                  stream=None) -> dict:
         """Times the compiled launch geometries (tile shape, pipeline depth,
         CTAs per SM) on these frames and keeps the fastest (``nrm_autotune``;
-        cached in ``cache_path`` when given); returns the chosen configuration."""
+        cached in ``cache_path``, or in the process-wide file of
+        ``set_autotune_cache`` when None); returns the chosen configuration."""
         arr, _ = self.make_frames(items, outputs)
         cp = cache_path.encode() if cache_path else None
         _lib.check(self.lib.nrm_autotune(self.h, arr, len(items), _stream_ptr(stream), cp), "nrm_autotune")

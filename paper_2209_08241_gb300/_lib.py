@@ -101,6 +101,10 @@ SIGNATURES = [
     ("nrm_get_config", ctypes.c_int, [_H, ctypes.POINTER(TileConfig)]),
     ("nrm_set_config", ctypes.c_int, [_H, ctypes.POINTER(TileConfig)]),
     ("nrm_autotune", ctypes.c_int, [_H, ctypes.POINTER(Frame), ctypes.c_int, _S, ctypes.c_char_p]),
+    ("nrm_set_autotune_cache", ctypes.c_int, [ctypes.c_char_p]),
+    ("nrm_autotune_key", ctypes.c_int, [_H, ctypes.c_char_p, ctypes.c_int]),
+    ("nrm_autotune_cache_get", ctypes.c_int, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(TileConfig)]),
+    ("nrm_autotune_cache_put", ctypes.c_int, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(TileConfig)]),
     ("nrm_enable_timing", ctypes.c_int, [_H, ctypes.c_int]),
     ("nrm_get_stats", ctypes.c_int, [_H, ctypes.POINTER(Stats)]),
     ("nrm_reset_stats", ctypes.c_int, [_H]),

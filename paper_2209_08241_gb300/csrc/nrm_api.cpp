@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <fstream>
 #include <map>
@@ -70,64 +71,61 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // Looked up once (thread-safe static initialisation).
+  static const EncodeTiledFn fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
+      return reinterpret_cast<EncodeTiledFn>(p);
+    return static_cast<EncodeTiledFn>(nullptr);
+  }();
   return fn;
+}
+
+// cuTensorMapEncodeTiled for a rank-2 or rank-3 map with unit element
+// strides, no interleave or swizzle, 256-byte L2 promotion and zero fill.
+bool encode_tiled(CUtensorMap* m, CUtensorMapDataType dtype, int rank, const void* base, const cuuint64_t* dims,
+                  const cuuint64_t* strides, const cuuint32_t* box) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, dtype, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
 }
 
 // Encodes a 2-D tiled map of a depth image with box (box_w x box_h) elements,
 // zero fill outside the image. Returns false if the map cannot be made.
 bool encode_depth_map(CUtensorMap* m, const void* base, int in_dtype, int W, int H, long long pitch,
                       int box_w, int box_h) {
-  EncodeTiledFn fn = encode_fn();
-  if (!fn) return false;
   const int eb = in_dtype == NRM_IN_U16_MM ? 2 : 4;
-  cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
-  cuuint64_t strides[1] = {(cuuint64_t)pitch * (cuuint64_t)eb};
-  cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
-  cuuint32_t es[2] = {1, 1};
-  CUresult r = fn(m, in_dtype == NRM_IN_U16_MM ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                  2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
+  const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch * (cuuint64_t)eb};
+  const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+  return encode_tiled(m, in_dtype == NRM_IN_U16_MM ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                      2, base, dims, strides, box);
 }
 
 // Upstream gradient of the adjoint (float4 per pixel) as a 3-D float32 tensor
 // (4, W, H); box (4, box_w, box_h) lands in shared memory as float4 per pixel.
 bool encode_grad_map(CUtensorMap* m, const void* base, int W, int H, long long out_pitch, int box_w,
                      int box_h) {
-  EncodeTiledFn fn = encode_fn();
-  if (!fn || (uintptr_t)base % 16) return false;
-  cuuint64_t dims[3] = {4, (cuuint64_t)W, (cuuint64_t)H};
-  cuuint64_t strides[2] = {16, (cuuint64_t)out_pitch * 16};
-  cuuint32_t box[3] = {4, (cuuint32_t)box_w, (cuuint32_t)box_h};
-  cuuint32_t es[3] = {1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  if ((uintptr_t)base % 16) return false;
+  const cuuint64_t dims[3] = {4, (cuuint64_t)W, (cuuint64_t)H};
+  const cuuint64_t strides[2] = {16, (cuuint64_t)out_pitch * 16};
+  const cuuint32_t box[3] = {4, (cuuint32_t)box_w, (cuuint32_t)box_h};
+  return encode_tiled(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box);
 }
 
 // The mask (one byte per pixel, pitch out_pitch) as a 2-D uint8 tensor.
 bool encode_mask_map(CUtensorMap* m, const void* base, int W, int H, long long out_pitch, int box_w, int box_h) {
-  EncodeTiledFn fn = encode_fn();
-  if (!fn || (uintptr_t)base % 16 || out_pitch % 16) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
-  cuuint64_t strides[1] = {(cuuint64_t)out_pitch};
-  cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
-  cuuint32_t es[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  if ((uintptr_t)base % 16 || out_pitch % 16) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+  const cuuint64_t strides[1] = {(cuuint64_t)out_pitch};
+  const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+  return encode_tiled(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box);
 }
 
 bool finite_positive(double v) { return std::isfinite(v) && v > 0.0; }
@@ -285,6 +283,8 @@ struct nrm_handle {
   HostLane lanes[kLanes];             // nrm_estimate_batched_host pipeline
   cudaEvent_t host_start = nullptr;
   std::vector<FrameDesc> scratch_desc;
+  std::vector<int> scratch_tb;               // tile_begin of a parameter-block launch
+  std::vector<unsigned char> scratch_param;  // its packed parameter block (+128 for alignment)
 };
 
 namespace {
@@ -529,10 +529,10 @@ std::map<std::string, std::string> read_cache(const char* path) {
   return m;
 }
 
-void write_cache(const char* path, const std::map<std::string, std::string>& m) {
+bool write_cache(const char* path, const std::map<std::string, std::string>& m) {
   std::string tmp = std::string(path) + ".tmp";
   std::ofstream out(tmp);
-  if (!out) return;
+  if (!out) return false;
   out << "{\n";
   size_t n = 0;
   for (const auto& kv : m) {
@@ -540,7 +540,8 @@ void write_cache(const char* path, const std::map<std::string, std::string>& m) 
   }
   out << "}\n";
   out.close();
-  std::rename(tmp.c_str(), path);
+  if (!out) return false;
+  return std::rename(tmp.c_str(), path) == 0;
 }
 
 std::string tune_key(const nrm_handle* h, const nrm_frame* f, int n) {
@@ -564,11 +565,47 @@ std::string tune_key(const nrm_handle* h, const nrm_frame* f, int n) {
   return k.str();
 }
 
+// The key of a handle as created: GPU, SM count, input dtype of its params,
+// output dtype, alpha and the handle's frame size (0 x 0 for batch handles).
+std::string handle_key(const nrm_handle* h) {
+  std::string name = h->gpu_name;
+  for (auto& ch : name)
+    if (ch == '"' || ch == '\\') ch = '_';
+  std::ostringstream k;
+  k << name << "|sm" << h->sm_count << "|in" << (1 << h->p.in_dtype) << "|out" << h->p.out_dtype << "|a"
+    << h->p.alpha << "|handle" << h->H << "x" << h->W;
+  return k.str();
+}
+
+std::mutex g_tune_mu;            // guards g_tune_path and the cache files this process writes
+std::string g_tune_path;         // process-wide cache file ("" = none)
+bool g_tune_path_set = false;    // set by nrm_set_autotune_cache (else the environment decides)
+
+std::string tune_path(const char* explicit_path) {
+  if (explicit_path) return explicit_path;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (g_tune_path_set) return g_tune_path;
+  const char* env = std::getenv("NRM_AUTOTUNE_CACHE");
+  return env ? env : "";
+}
+
+bool parse_config(const std::string& v, nrm_tile_config* c) {
+  return std::sscanf(v.c_str(), "%d , %d , %d , %d , %d", &c->tile_x, &c->tile_y, &c->threads, &c->stages,
+                     &c->ctas_per_sm) == 5;
+}
+
+std::string format_config(const nrm_tile_config& c) {
+  char buf[128];
+  std::snprintf(buf, sizeof(buf), "%d, %d, %d, %d, %d", c.tile_x, c.tile_y, c.threads, c.stages, c.ctas_per_sm);
+  return buf;
+}
+
 }  // namespace
 
 namespace nrm {
 
 int host_fail(int code, const char* message) { return fail(code, "%s", message); }
+void host_clear_error() { g_last_error.clear(); }
 int host_validate_params(const nrm_params& p) { return validate_params(p); }
 int host_validate_frame(const nrm_frame& f, int index, int out_dtype) { return validate_frame(f, index, out_dtype); }
 void host_make_forward_desc(FrameDesc* d, const nrm_frame& f, const nrm_params& p, int tile_x, int tile_y) {
@@ -677,7 +714,66 @@ int nrm_create(const nrm_intrinsics* K, int H, int W, const nrm_params* p, nrm_h
     g_last_error = msg;
     return rc;
   }
+  // A tuned geometry for this handle's key from the process-wide cache file.
+  const std::string path = tune_path(nullptr);
+  if (!path.empty()) {
+    std::map<std::string, std::string> cache;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      cache = read_cache(path.c_str());
+    }
+    auto it = cache.find(handle_key(h));
+    nrm_tile_config tuned;
+    if (it != cache.end() && parse_config(it->second, &tuned) && configure(h, tuned) != NRM_OK) {
+      configure(h, c);  // a stale or foreign entry: keep the default geometry
+      g_last_error.clear();
+    }
+  }
   *out = h;
+  return NRM_OK;
+}
+
+int nrm_set_autotune_cache(const char* path) {
+  g_last_error.clear();
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_path = path ? path : "";
+  g_tune_path_set = true;
+  return NRM_OK;
+}
+
+int nrm_autotune_key(const nrm_handle* h, char* buf, int len) {
+  g_last_error.clear();
+  if (!h || !buf || len <= 0) return fail(NRM_ERR_INVALID_ARG, "bad arguments");
+  const std::string k = handle_key(h);
+  if ((int)k.size() + 1 > len) return fail(NRM_ERR_INVALID_ARG, "key needs %d bytes", (int)k.size() + 1);
+  std::memcpy(buf, k.c_str(), k.size() + 1);
+  return NRM_OK;
+}
+
+int nrm_autotune_cache_get(const char* path, const char* key, nrm_tile_config* cfg) {
+  g_last_error.clear();
+  if (!path || !key || !cfg) return fail(NRM_ERR_INVALID_ARG, "bad arguments");
+  std::map<std::string, std::string> cache;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    cache = read_cache(path);
+  }
+  auto it = cache.find(key);
+  if (it == cache.end()) return fail(NRM_ERR_INVALID_ARG, "no entry for this key in %s", path);
+  nrm_tile_config c;
+  if (!parse_config(it->second, &c)) return fail(NRM_ERR_INVALID_ARG, "malformed entry in %s", path);
+  *cfg = c;
+  return NRM_OK;
+}
+
+int nrm_autotune_cache_put(const char* path, const char* key, const nrm_tile_config* cfg) {
+  g_last_error.clear();
+  if (!path || !key || !cfg) return fail(NRM_ERR_INVALID_ARG, "bad arguments");
+  if (std::strpbrk(key, "\"\\")) return fail(NRM_ERR_INVALID_ARG, "key contains a quote or a backslash");
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  std::map<std::string, std::string> cache = read_cache(path);
+  cache[key] = format_config(*cfg);
+  if (!write_cache(path, cache)) return fail(NRM_ERR_INVALID_ARG, "cannot write %s", path);
   return NRM_OK;
 }
 
@@ -776,8 +872,10 @@ static int estimate_batched_param(nrm_handle* h, const nrm_frame* frames, int n,
   if (n > nrm::kParamMaxFrames)
     return fail(NRM_ERR_UNSUPPORTED, "at most %d frames per call during stream capture", nrm::kParamMaxFrames);
   const int TX = h->cfg.tile_x, TY = h->cfg.tile_y;
-  std::vector<FrameDesc> fd((size_t)n);
-  std::vector<int> tb((size_t)n + 1);
+  std::vector<FrameDesc>& fd = h->scratch_desc;
+  std::vector<int>& tb = h->scratch_tb;
+  if (fd.size() < (size_t)n) fd.resize((size_t)n);
+  if (tb.size() < (size_t)n + 1) tb.resize((size_t)n + 1);
   bool u16 = true;
   int acc = 0;
   for (int i = 0; i < n; ++i) {
@@ -798,7 +896,8 @@ static int estimate_batched_param(nrm_handle* h, const nrm_frame* frames, int n,
   hdr.n_frames = n;
   hdr.total_tiles = acc;
   // The parameter block, 128-byte aligned like the records in it.
-  std::vector<unsigned char> raw(nrm::param_batch_bytes() + 128);
+  std::vector<unsigned char>& raw = h->scratch_param;
+  if (raw.size() < nrm::param_batch_bytes() + 128) raw.resize(nrm::param_batch_bytes() + 128);
   void* pb = raw.data() + (128 - reinterpret_cast<uintptr_t>(raw.data()) % 128) % 128;
   nrm::pack_param_batch(pb, hdr, tb.data(), fd.data(), n);
   nrm::BatchArgs ring;
@@ -1514,17 +1613,16 @@ int nrm_autotune(nrm_handle* h, const nrm_frame* frames, int n, void* cuda_strea
   if (n == 0) return NRM_OK;
   DeviceGuard guard(h->device);
   const std::string key = tune_key(h, frames, n);
+  const std::string path = tune_path(cache_path);
   std::map<std::string, std::string> cache;
-  if (cache_path) {
-    cache = read_cache(cache_path);
-    auto it = cache.find(key);
-    if (it != cache.end()) {
-      nrm_tile_config c;
-      if (std::sscanf(it->second.c_str(), "%d , %d , %d , %d , %d", &c.tile_x, &c.tile_y, &c.threads, &c.stages,
-                      &c.ctas_per_sm) == 5 &&
-          configure(h, c) == NRM_OK)
-        return NRM_OK;
+  if (!path.empty()) {
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      cache = read_cache(path.c_str());
     }
+    auto it = cache.find(key);
+    nrm_tile_config c;
+    if (it != cache.end() && parse_config(it->second, &c) && configure(h, c) == NRM_OK) return NRM_OK;
   }
   const bool timing_was = h->timing;
   h->timing = false;
@@ -1588,12 +1686,12 @@ int nrm_autotune(nrm_handle* h, const nrm_frame* frames, int n, void* cuda_strea
   int rc2 = configure(h, rc == NRM_OK ? best : start);
   if (rc) return rc;
   if (rc2) return rc2;
-  if (cache_path) {
-    char buf[128];
-    std::snprintf(buf, sizeof(buf), "%d, %d, %d, %d, %d", best.tile_x, best.tile_y, best.threads, best.stages,
-                  best.ctas_per_sm);
-    cache[key] = buf;
-    write_cache(cache_path, cache);
+  if (!path.empty()) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    cache = read_cache(path.c_str());  // entries other processes added meanwhile
+    cache[key] = format_config(best);
+    cache[handle_key(h)] = format_config(best);
+    write_cache(path.c_str(), cache);
   }
   return NRM_OK;
 }

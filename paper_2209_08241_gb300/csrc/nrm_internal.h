@@ -148,6 +148,7 @@ NRM_HD inline int persistent_threads(int compute_threads) { return compute_threa
 // validation (sets the thread-local error message) and descriptor filling for
 // the forward kernels with tile (tile_x, tile_y).
 int host_fail(int code, const char* message);
+void host_clear_error();  // clears the thread's last-error message, as every entry point does first
 int host_validate_params(const nrm_params& p);
 int host_validate_frame(const nrm_frame& f, int index, int out_dtype);
 void host_make_forward_desc(FrameDesc* d, const nrm_frame& f, const nrm_params& p, int tile_x, int tile_y);
