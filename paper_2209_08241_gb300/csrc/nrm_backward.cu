@@ -56,6 +56,10 @@ __host__ __device__ inline unsigned weight_tile_bytes(int alpha) {
 __host__ __device__ inline unsigned mask_tile_bytes(int alpha) {
   return round128((unsigned)(MW * (TY + 2 * alpha)));
 }
+// u1 of each column and v1 of each row of the extended region.
+__host__ __device__ inline unsigned coord_table_bytes(int alpha) {
+  return round128((unsigned)((TX + TY + 4 * alpha) * 4));
+}
 
 // One output tile (gx0, gy0) of frame fd. tmap_d/tmap_g/tmap_m: its depth,
 // gradient and mask tensor maps (param or global memory; used only when
@@ -76,9 +80,19 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d
   float* dep = reinterpret_cast<float*>(smem);
   float4* gw = reinterpret_cast<float4*>(smem + depth_tile_bytes(alpha));
   uint8_t* msk = smem + depth_tile_bytes(alpha) + weight_tile_bytes(alpha);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(msk + mask_tile_bytes(alpha));
+  float* ucol = reinterpret_cast<float*>(msk + mask_tile_bytes(alpha));  // u1 of extended column ex
+  float* vrow = ucol + ex_w;                                              // v1 of extended row ey
+  uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(ucol) + coord_table_bytes(alpha));
   const int H = fd.H, W = fd.W;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // The ray coordinates of the extended region, formed while the copies are
+  // in flight (the barrier that follows them publishes these too).
+  for (int t = threadIdx.x; t < ex_w + ex_h; t += NT) {
+    if (t < ex_w)
+      ucol[t] = ((float)(gx0 - alpha + t) - fd.cx) * fd.inv_fx;
+    else
+      vrow[t - ex_w] = ((float)(gy0 - alpha + t - ex_w) - fd.cy) * fd.inv_fy;
+  }
 
   if (fd.use_tma) {
     const uint32_t b = smem_u32(bar);
@@ -122,7 +136,12 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d
   // order with stride NT, advancing (ey, ex) by increments (no division).
   // A pixel the forward marked valid has a positive finite five-point stencil
   // (that is what made it valid), so only the mask is consulted here.
-  const FrameConsts k = {fd.a, fd.b, fd.c, fd.inv_fx, fd.inv_fy, fd.cx, fd.cy};
+  // With A35 = a S35, B35 = b D35, C35 = c S35 and A24 = a D24, B24 = b S24,
+  // C24 = c S24, Eq. 4-6 read n_x = -A35 D24, n_y = -B24 D35, P = C24 S35, and
+  // the weights (e_x = h_x - u1 h_z, e_y = h_y - v1 h_z) are
+  //   w2 = -e_x A35 - e_y B35 + h_z C35,  w4 = e_x A35 - e_y B35 + h_z C35,
+  //   w3 = -e_x A24 - e_y B24 + h_z C24,  w5 = -e_x A24 + e_y B24 + h_z C24.
+  const float ka = fd.a, kb = fd.b, kc = fd.c;
   const int n_ext = ex_w * ex_h;
   const int step_rows = NT / ex_w, step_cols = NT - step_rows * ex_w;
   int ey = threadIdx.x / ex_w;
@@ -134,31 +153,29 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d
     if (msk_c[ey * MW + ex]) {
       const float* pc = dep_c + ey * bw + ex;
       const float d2 = pc[alpha], d4 = pc[-alpha], d3 = pc[alpha * bw], d5 = pc[-alpha * bw];
-      StencilSums s;
-      s.S24 = d2 + d4;
-      s.D24 = d2 - d4;
-      s.S35 = d3 + d5;
-      s.D35 = d3 - d5;
-      const float u1 = ((float)(gx0 - alpha + ex) - k.cx) * k.inv_fx;
-      const float v1 = ((float)(gy0 - alpha + ey) - k.cy) * k.inv_fy;
-      float nx, ny, nz, P;
-      closed_form_normal(s, k, u1, v1, nx, ny, nz, P);
+      const float S24 = d2 + d4, D24 = d2 - d4, S35 = d3 + d5, D35 = d3 - d5;
+      const float u1 = ucol[ex], v1 = vrow[ey];
+      const float A35 = ka * S35, B35 = kb * D35, C35 = kc * S35;
+      const float A24 = ka * D24, B24 = kb * S24, C24 = kc * S24;
+      const float nx = -A35 * D24, ny = -B24 * D35, P = C24 * S35;
+      const float nz = fmaf(-u1, nx, fmaf(-v1, ny, P));
       const float q = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
       const float inv = rsqrt_ftz(fmaxf(q, 1.17549435e-38f));
       const float hx0 = nx * inv, hy0 = ny * inv, hz0 = nz * inv;
       const float4 gv = gw[i];
       const float gd = fmaf(gv.x, hx0, fmaf(gv.y, hy0, gv.z * hz0));
       const float si = g.sign * inv;
-      const float hx = (gv.x - gd * hx0) * si;
-      const float hy = (gv.y - gd * hy0) * si;
-      const float hz = (gv.z - gd * hz0) * si;
-      const float ex_ = fmaf(-u1, hz, hx);
-      const float ey_ = fmaf(-v1, hz, hy);
-      const float ea = ex_ * k.a, eb = ey_ * k.b, hc = hz * k.c;
-      w.x = -ea * s.S35 - eb * s.D35 + hc * s.S35;  // w2
-      w.y = -ea * s.D24 - eb * s.S24 + hc * s.S24;  // w3
-      w.z = ea * s.S35 - eb * s.D35 + hc * s.S35;   // w4
-      w.w = -ea * s.D24 + eb * s.S24 + hc * s.S24;  // w5
+      const float hx = fmaf(-gd, hx0, gv.x) * si;
+      const float hy = fmaf(-gd, hy0, gv.y) * si;
+      const float hz = fmaf(-gd, hz0, gv.z) * si;
+      const float e_x = fmaf(-u1, hz, hx);
+      const float e_y = fmaf(-v1, hz, hy);
+      const float c35 = fmaf(hz, C35, -e_y * B35);
+      const float c24 = fmaf(hz, C24, -e_x * A24);
+      w.x = fmaf(-e_x, A35, c35);  // w2
+      w.y = fmaf(-e_y, B24, c24);  // w3
+      w.z = fmaf(e_x, A35, c35);   // w4
+      w.w = fmaf(e_y, B24, c24);   // w5
     }
     gw[i] = w;
     ey += step_rows;
@@ -276,7 +293,7 @@ cudaError_t set_smem(const void* fn, unsigned bytes) {
 }  // namespace
 
 unsigned bwd_smem_bytes(int alpha) {
-  return depth_tile_bytes(alpha) + weight_tile_bytes(alpha) + mask_tile_bytes(alpha) + 16;
+  return depth_tile_bytes(alpha) + weight_tile_bytes(alpha) + mask_tile_bytes(alpha) + coord_table_bytes(alpha) + 16;
 }
 
 cudaError_t launch_backward(const FrameDesc& fd, const BwdMaps& maps, const Globals& g, cudaStream_t stream) {
