@@ -18,9 +18,21 @@ bounded sample of the same frames on this host's cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-With N > 1 (launched by torchrun) every rank runs its own batch of 64 frames
-(frames are independent: weak scaling, no collective on the data path) and
-rank 0 reports the total pixels of all ranks over the slowest rank's time.
+With N > 1 (launched by torchrun) the global batch is N x 64 frames, split
+over the ranks by the pixel-balanced frame partition of the package
+(``partition.balance_frames``; frames are independent, so there is no
+collective on the data path: weak scaling), and rank 0 reports the total pixels
+of all ranks over the slowest rank's time. The uneven 256-frame mix is split
+the same way (strong scaling of that batch).
+
+``cpu_baseline`` is the CPU leg: the oracle timed on this host's cores, and the
+same oracle run over every frame of the headline batch and of the uneven mix,
+compared pixel by pixel with the GPU's results of those frames (``parity``:
+largest angular error, mask mismatches outside the 1e-6 band around tau, and
+the pixels inside that band, counted).
+
+``--kernel-case CASE`` instead runs one kernel on synthetic input for timing
+and profiling (see ``kernel_case``).
 """
 from __future__ import annotations
 
@@ -42,12 +54,19 @@ UNIT = "Mpixel/s"
 N_FRAMES, W_FULLHD, H_FULLHD = 64, 1920, 1080
 BYTES_PER_PX = 2 + 16 + 1       # uint16 depth in, float4 normal + uint8 mask out
 KERNEL_SOURCES = ("paper_2209_08241_gb300/csrc/nrm_forward.cu", "paper_2209_08241_gb300/csrc/nrm_forward_param.cu",
-                  "paper_2209_08241_gb300/csrc/nrm_forward_kernels.cuh", "paper_2209_08241_gb300/csrc/nrm_device.cuh")
+                  "paper_2209_08241_gb300/csrc/nrm_forward_kernels.cuh", "paper_2209_08241_gb300/csrc/nrm_device.cuh",
+                  "paper_2209_08241_gb300/csrc/nrm_forward_vec.cuh")
 
 # DRAM bytes per launch of the batched kernel from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum), valid only while the kernel sources hash to the key.
-# Measured on the 64 x 1080p uint16 workload (profiles/fwd_persistent_u16_64x1080p.md).
-NCU_TRAFFIC = {"4347f3f8573869bd": 2460557312}
+# dram__bytes_write.sum) on the 64 x 1080p uint16 workload, valid only while
+# the kernel sources hash to the key (otherwise the line reports null).
+NCU_TRAFFIC = {}
+
+# Parity tolerances (normals: angle to the FP64 oracle's; masks: exact except
+# pixels whose oracle statistic lies within NEAR_TAU_REL of tau).
+ANG_TOL = {"f32": 1e-4, "f16": 5e-3}
+NEAR_TAU_REL = 1e-6
+TAU = 12.0
 
 
 def kernel_source_hash() -> str:
@@ -207,6 +226,94 @@ def time_oracle_on(frames_np, K, cores, budget_s=12.0, max_frames=4096):
     return done_px / dt / 1e6, nfr, dt
 
 
+def parity_frame(normals, valid, depth, K, depth_scale, cores, acc):
+    """Compares one GPU result (normals H x W x 4, float32 or half; valid H x W)
+    with the FP64 oracle on the same depth and accumulates the counts in acc."""
+    import numpy as np
+
+    import oracle
+    ref = oracle.forward(depth, K, alpha=2, stat_mode=oracle.STAT_SECANT, tau=TAU, depth_scale=depth_scale,
+                         nthreads=cores)
+    n = normals.astype(np.float64)
+    m = valid.astype(np.uint8)
+    with np.errstate(invalid="ignore"):
+        near = np.isfinite(ref.stat) & (np.abs(ref.stat - TAU) <= NEAR_TAU_REL * TAU)
+    acc["pixels"] += int(m.size)
+    acc["near_tau_pixels"] += int(near.sum())
+    acc["mask_mismatches_outside_band"] += int(((m != ref.valid) & ~near).sum())
+    acc["mask_bytes_not_0_or_1"] += int((m > 1).sum())
+    acc["masked_pixels_not_zero"] += int((n[m == 0] != 0).any(axis=-1).sum())
+    both = (m == 1) & (ref.valid == 1)
+    acc["valid_pixels_compared"] += int(both.sum())
+    if both.any():
+        a = n[both][:, :3]
+        b = ref.n_hat[both]
+        # sin of the angle: |a x b| / (|a| |b|) (accurate for small angles)
+        s = np.linalg.norm(np.cross(a, b), axis=-1) / (np.linalg.norm(a, axis=-1) * np.linalg.norm(b, axis=-1))
+        dot_neg = (np.sum(a * b, axis=-1) < 0).sum()
+        ang = float(np.arcsin(min(1.0, float(s.max())))) if not dot_neg else float(np.pi)
+        acc["max_angle_rad"] = max(acc["max_angle_rad"], ang)
+
+
+def new_parity(out: str, frames: int) -> dict:
+    return {"frames": frames, "out": out, "pixels": 0, "valid_pixels_compared": 0, "max_angle_rad": 0.0,
+            "tolerance_rad": ANG_TOL[out], "mask_mismatches_outside_band": 0, "near_tau_pixels": 0,
+            "near_tau_rel": NEAR_TAU_REL, "mask_bytes_not_0_or_1": 0, "masked_pixels_not_zero": 0}
+
+
+def finish_parity(acc: dict) -> dict:
+    acc["max_angle_rad"] = float(f"{acc['max_angle_rad']:.3g}")
+    acc["pass"] = (acc["mask_mismatches_outside_band"] == 0 and acc["max_angle_rad"] <= acc["tolerance_rad"]
+                   and acc["mask_bytes_not_0_or_1"] == 0 and acc["masked_pixels_not_zero"] == 0)
+    return acc
+
+
+def cpu_leg(dev, depth, Ks, normals, valid, n_frames, stream):
+    """The CPU leg (rank 0, N = 1 workload): the FP64 oracle timed on this
+    host's cores on a bounded sample of the headline frames, then run over
+    every headline frame and every frame of the uneven 256-frame float32 mix
+    and compared with the GPU's results of the same frames (parity records)."""
+    import torch
+
+    import paper_2209_08241_gb300 as nrm
+    from synth import scenes
+
+    cores = cpu_cores()
+    frames_np = [depth[i].cpu().numpy() for i in range(min(4, n_frames))]
+    mpx, nfr, dt = time_oracle_on(frames_np, Ks[0], cores, budget_s=10.0)
+    mpx1, nfr1, dt1 = time_oracle_on(frames_np, Ks[0], 1, budget_s=4.0)
+    cpu = {"value": round(mpx, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{nfr} full-HD uint16 frames cycling over the first {len(frames_np)} of the batch "
+                     f"({nfr * H_FULLHD * W_FULLHD} px), FP64 direct form, {cores} threads, {dt:.1f} s",
+           "single_thread": {"value": round(mpx1, 3), "unit": UNIT, "frames": nfr1, "seconds": round(dt1, 2)},
+           "cpu_model": cpu_model()}
+    t0 = time.perf_counter()
+    # The headline batch: the outputs of the last timed step.
+    torch.cuda.synchronize(dev)
+    acc = new_parity("f32", n_frames)
+    for i in range(n_frames):
+        parity_frame(normals[i].cpu().numpy(), valid[i].cpu().numpy(), depth[i].cpu().numpy(), Ks[i], 0.001,
+                     cores, acc)
+    parity = {"headline_64x1080p_u16_f32out": finish_parity(acc)}
+    # The uneven 256-frame float32 mix, float4 and half4 outputs (one batched
+    # launch each, default geometry).
+    mix = scenes.mixed_batch(256, device=dev, kind="f32")
+    for od in ("f32", "f16"):
+        b = nrm.BatchedEstimator(nrm.NormalParams(out_dtype=od), device=dev)
+        outs = b(mix, stream=stream)
+        torch.cuda.synchronize(dev)
+        b.sync_status()
+        acc = new_parity(od, len(mix))
+        for (d, K), (nm, vm) in zip(mix, outs):
+            parity_frame(nm.float().cpu().numpy(), vm.cpu().numpy(), d.cpu().numpy(), K, 1.0, cores, acc)
+        parity[f"mixed256_f32in_{od}out"] = finish_parity(acc)
+        del b, outs
+    del mix
+    torch.cuda.empty_cache()
+    parity["seconds"] = round(time.perf_counter() - t0, 1)
+    return cpu, parity
+
+
 def bench_ours(args, dist: Dist):
     import torch
     N_FRAMES = args.frames
@@ -214,13 +321,23 @@ def bench_ours(args, dist: Dist):
     import paper_2209_08241_gb300 as nrm
     from synth import scenes
 
+    from paper_2209_08241_gb300 import partition
+
     torch.cuda.set_device(dist.local_rank)
     dev = torch.device("cuda", dist.local_rank)
-    # This rank's batch: frames are independent, seeds differ per rank.
+    # Tuned launch geometries are recorded in this file and reused by later
+    # processes on the same GPU model (handles start from them; the sweep is
+    # skipped for a batch whose key is recorded).
+    nrm.set_autotune_cache(os.path.join(ROOT, "paper_2209_08241_gb300", "_build", "autotune_cache.json"))
+    # This rank's share of the global batch of N x 64 frames (frame g has seed
+    # 1000 + g), from the pixel-balanced split every rank computes alike.
+    global_px = [H_FULLHD * W_FULLHD] * (N_FRAMES * dist.world)
+    mine = partition.rank_frames(global_px, dist.rank, dist.world)
+    N_FRAMES = len(mine)
     depth = torch.empty((N_FRAMES, H_FULLHD, W_FULLHD), dtype=torch.uint16, device=dev)
     Ks = []
-    for i in range(N_FRAMES):
-        d, K = scenes.random_frame(1000 + N_FRAMES * dist.rank + i, W_FULLHD, H_FULLHD, dev, kind="u16")
+    for i, gidx in enumerate(mine):
+        d, K = scenes.random_frame(1000 + gidx, W_FULLHD, H_FULLHD, dev, kind="u16")
         depth[i].copy_(d)
         Ks.append(K)
     normals = torch.empty((N_FRAMES, H_FULLHD, W_FULLHD, 4), dtype=torch.float32, device=dev)
@@ -244,8 +361,8 @@ def bench_ours(args, dist: Dist):
     est.enable_timing(True)
     clocks = ClockSampler(dist.local_rank)
     clocks.start()
-    # Warm-up: at least W steps and at least one second of work (so that the
-    # clock sampler sees the GPU under load).
+    # Warm-up: W steps, then more until one second has passed (so that the
+    # clock sampler sees the GPU under load); the line reports both counts.
     t_w = time.time()
     w = 0
     while w < args.warmup or time.time() - t_w < 1.0:
@@ -254,6 +371,7 @@ def bench_ours(args, dist: Dist):
         if w % 50 == 0:
             torch.cuda.synchronize(dev)
     torch.cuda.synchronize(dev)
+    warmup_s = time.time() - t_w
     est.reset_stats()
     dist.barrier()
     torch.cuda.synchronize(dev)
@@ -319,31 +437,27 @@ def bench_ours(args, dist: Dist):
         est.enable_timing(True)
 
     extra = {}
-    if not args.skip_extra:
+    if dist.world > 1:
+        # Several GPUs: the uneven mix split over the ranks (the only extra).
+        if not args.skip_extra:
+            extra = bench_sharded_mix(args, dist, nrm, scenes, partition, dev, stream)
+    elif not args.skip_extra:
         extra = bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames, dev, stream,
                              N_FRAMES)
 
     serving = None
-    if not args.skip_serving:
+    if not args.skip_serving and dist.world == 1:
         rates = (1, 10, 100, 1000, 4000, 8000) if args.serving_full else (100, 1000, 4000, 8000)
         serving = bench_serving(args, dev, rates, 60.0 if args.serving_full else 2.0)
 
-    cpu = None
-    if dist.rank == 0 and not args.skip_cpu:
-        cores = cpu_cores()
-        frames_np = [depth[i].cpu().numpy() for i in range(min(4, N_FRAMES))]
-        mpx, nfr, dt = time_oracle_on(frames_np, Ks[0], cores, budget_s=10.0)
-        mpx1, nfr1, dt1 = time_oracle_on(frames_np, Ks[0], 1, budget_s=4.0)
-        cpu = {"value": round(mpx, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{nfr} full-HD uint16 frames cycling over the first {len(frames_np)} of the batch "
-                         f"({nfr * H_FULLHD * W_FULLHD} px), "
-                         f"FP64 direct form, {cores} threads, {dt:.1f} s",
-               "single_thread": {"value": round(mpx1, 3), "unit": UNIT, "frames": nfr1, "seconds": round(dt1, 2)},
-               "cpu_model": cpu_model()}
+    cpu, parity = None, None
+    if dist.rank == 0 and dist.world == 1 and not args.skip_cpu:
+        cpu, parity = cpu_leg(dev, depth, Ks, normals, valid, N_FRAMES, stream)
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": dist.world,
         "steps": args.steps, "warmup": w, "ms_per_step": round(ms_per_step, 4),
+        "warmup_rule": f"at least --warmup={args.warmup} steps and at least 1 s ({w} steps, {warmup_s:.2f} s)",
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
         "data": "synthetic (seeded random-primitive scenes, Kinect-style noise, 1 mm quantisation, 2% holes)",
         "config": {**workload_config(N_FRAMES), "launch": "one batched persistent launch per step",
@@ -354,7 +468,7 @@ def bench_ours(args, dist: Dist):
                            + ("" if (args.no_autotune or args.config) else " (autotuned)"),
                    "parallelism": f"frame-sharded x{dist.world} (no collective)",
                    "l2": f"inputs larger than L2 ({px_per_step * BYTES_PER_PX / 1e6:.0f} MB moved per step)"},
-        "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "parity": parity,
         "clocks": clocks.summary(), "gpu_launches": args.steps,
         "extra": extra, "serving": serving,
     }
@@ -727,6 +841,37 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
     return out
 
 
+def bench_sharded_mix(args, dist, nrm, scenes, partition, dev, stream):
+    """The uneven 256-frame float32 mix split over the ranks by pixels (each
+    rank builds only its frames, seed 3000 + frame index, as in
+    scenes.mixed_batch); one batched launch per rank and step; total pixels
+    over the slowest rank's time."""
+    import torch
+    sizes = scenes.size_mix(256, 3)
+    mine = partition.rank_frames([w * h for w, h in sizes], dist.rank, dist.world)
+    items = [scenes.random_frame(3000 + i, sizes[i][0], sizes[i][1], dev, kind="f32") for i in mine]
+    b = nrm.BatchedEstimator(nrm.NormalParams(), device=dev)
+    outs = b(items, stream=stream)
+    fr, _ = b.make_frames(items, outs)
+    reps = max(3, min(args.steps, 20))
+    for _ in range(3):
+        b.run(fr, len(items), stream)
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        b.run(fr, len(items), stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    t_max = dist.reduce(e0.elapsed_time(e1) / reps, "max")
+    px_all = dist.reduce(float(sum(d.numel() for d, _ in items)), "sum")
+    b.sync_status()
+    return {"mixed256_sharded_mpx_s": round(px_all / (t_max / 1e3) / 1e6, 1),
+            "mixed256_sharded_frames_per_rank": len(mine), "mixed256_sharded_scaling": "strong"}
+
+
 def _sig(t):
     """[MSE theta, MSE phi, count] of an angle_mse result, to 4 significant digits."""
     return [float(f"{float(v):.4g}") for v in t.tolist()]
@@ -879,14 +1024,133 @@ def bench_reference(args, dist: Dist):
     }
 
 
+# -------------------------------------------------------------- kernel cases
+
+KERNEL_CASES = ("forward", "adjoint", "adjoint_batch", "plane_fit", "multiscale", "multiscale_batch",
+                "spherical", "angle_mse")
+OUT_BYTES = {"f32": 16, "f16": 8, "oct16": 4}
+
+
+def kernel_case(args):
+    """Runs one kernel on synthetic input ``--reps`` times after one untimed
+    call and prints the mean time per call (CUDA events on the stream) and the
+    algorithmic bandwidth; for timing and for ncu captures. Cases:
+      forward           batched forward on --frames full-HD uint16 frames
+                        (default 8), normals as --out (f32, f16, oct16), launch
+                        geometry --config (default: the handle's)
+      adjoint           single-frame adjoint, 4096 x 3072 float32
+      adjoint_batch     batched adjoint, --frames 640 x 480 float32 (default 32)
+      plane_fit         plane-fitting ground truth, --radius, 4096 x 3072
+      multiscale        multi-scale alpha = 1..4, --form pair|quad, 4096 x 3072
+      multiscale_batch  the same batched on --frames full-HD uint16 frames
+      spherical         I_phi / I_theta images of a 4096 x 3072 normal map
+      angle_mse         angle-image MSE of two 4096 x 3072 normal maps
+    The batched cases time the kernel with the library's in-launch events."""
+    import torch
+
+    import paper_2209_08241_gb300 as nrm
+    from synth import scenes
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def big_frame():
+        return scenes.random_frame(4999, 4096, 3072, "cuda", kind="f32", holes=False, clip_range=False)
+
+    case, reps = args.kernel_case, args.reps
+    if case in ("forward", "multiscale_batch"):
+        frames = args.frames or 8
+        items = [scenes.random_frame(1000 + i, W_FULLHD, H_FULLHD, "cuda", kind="u16") for i in range(frames)]
+        b = nrm.BatchedEstimator(nrm.NormalParams(out_dtype=args.out if case == "forward" else "f32"))
+        if case == "forward":
+            outs = b(items)
+            if args.config:
+                b.set_config(*[int(v) for v in args.config.split(",")])
+            arr, _ = b.make_frames(items, outs)
+            b.enable_timing(True)
+            b.run(arr, frames)
+            torch.cuda.synchronize()
+            b.reset_stats()
+            for _ in range(reps):
+                b.run(arr, frames)
+            st = b.stats()
+            ms = st["kernel_ms"] / max(1, st["launches"])
+            nbytes_px = 2 + OUT_BYTES[args.out] + 1
+        else:
+            outs = b.multiscale(items, (1, 2, 3, 4), args.form)
+            arr, _ = b.make_frames(items, outs)
+            ms = timed(lambda: b.run_multiscale(arr, frames, (1, 2, 3, 4), args.form), reps)
+            nbytes_px = 19
+        b.sync_status()
+        px = frames * W_FULLHD * H_FULLHD
+    elif case == "adjoint":
+        d, K = big_frame()
+        est = nrm.NormalEstimator(K, 3072, 4096)
+        n, m = est(d)
+        g = torch.zeros_like(n)
+        g[..., 2] = m.float()
+        grad = torch.empty_like(d)
+        ms = timed(lambda: est.backward(d, g, m, grad), reps)
+        px, nbytes_px = 4096 * 3072, 25
+    elif case == "adjoint_batch":
+        frames = args.frames or 32
+        items = [scenes.random_frame(4000 + i, 640, 480, "cuda", kind="f32", holes=False, clip_range=False)
+                 for i in range(frames)]
+        b = nrm.BatchedEstimator()
+        outs = b(items)
+        gs = []
+        for n, m in outs:
+            g = torch.zeros_like(n)
+            g[..., 2] = m.float()
+            gs.append(g)
+        grads = [torch.empty_like(d) for d, _ in items]
+        arr, _ = b.make_grad_frames(items, gs, [m for _, m in outs], grads)
+        ms = timed(lambda: b.run_backward(arr, frames), reps)
+        px, nbytes_px = frames * 640 * 480, 25
+    elif case == "plane_fit":
+        d, K = big_frame()
+        est = nrm.NormalEstimator(K, 3072, 4096)
+        n, m = est.plane_fit(d, args.radius)
+        ms = timed(lambda: est.plane_fit(d, args.radius, n, m), reps)
+        px, nbytes_px = 4096 * 3072, 21
+    elif case == "multiscale":
+        d, K = big_frame()
+        est = nrm.NormalEstimator(K, 3072, 4096)
+        n, m = est.estimate_multiscale(d, (1, 2, 3, 4), args.form)
+        ms = timed(lambda: est.estimate_multiscale(d, (1, 2, 3, 4), args.form, n, m), reps)
+        px, nbytes_px = 4096 * 3072, 21
+    elif case == "spherical":
+        d, K = big_frame()
+        n, m = nrm.NormalEstimator(K, 3072, 4096)(d)
+        ms = timed(lambda: nrm.spherical_images(n, m), reps)
+        px, nbytes_px = 4096 * 3072, 25
+    else:  # angle_mse
+        d, K = big_frame()
+        est = nrm.NormalEstimator(K, 3072, 4096)
+        n, m = est(d)
+        rn, rm = est(torch.roll(d, 1, dims=0).contiguous())
+        ms = timed(lambda: nrm.angle_mse(est, n, m, rn, rm), reps)
+        px, nbytes_px = 4096 * 3072, 34
+    print(f"{case}: {ms:.4f} ms/call, {px / ms / 1e3:.1f} Mpx/s, {px * nbytes_px / ms / 1e6:.1f} GB/s algorithmic",
+          flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--frames", type=int, default=N_FRAMES,
-                    help="frames per GPU (default 64; smaller only for profiling)")
+    ap.add_argument("--frames", type=int, default=None,
+                    help="frames per GPU (default 64; smaller only for profiling); kernel cases: their batch size")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--config", default="", help="tile_x,tile_y,threads,stages[,ctas_per_sm] (skips the autotuner)")
     # The --skip-* switches leave out whole secondary measurements (for short
@@ -897,7 +1161,18 @@ def main(argv=None):
     ap.add_argument("--skip-serving", action="store_true", help="omit the serving sweep")
     ap.add_argument("--serving-full", action="store_true",
                     help="serving sweep at 1..8000 frames/s, 60 s each (default: 100..8000, 2 s each)")
+    ap.add_argument("--kernel-case", choices=KERNEL_CASES, default=None,
+                    help="run one kernel for timing or profiling instead of the benchmark")
+    ap.add_argument("--out", choices=sorted(OUT_BYTES), default="f32", help="normal output type (forward case)")
+    ap.add_argument("--reps", type=int, default=20, help="timed calls (kernel cases)")
+    ap.add_argument("--radius", type=int, default=2, help="window radius (plane_fit case)")
+    ap.add_argument("--form", choices=["pair", "quad"], default="pair", help="stencil (multiscale cases)")
     args = ap.parse_args(argv)
+    if args.kernel_case:
+        kernel_case(args)
+        return
+    if args.frames is None:
+        args.frames = N_FRAMES
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     dist = Dist()
