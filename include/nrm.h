@@ -204,6 +204,19 @@ typedef struct {
  * stream is being captured. */
 NRM_API int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, void* cuda_stream);
 
+/* nrm_backward_batched with the upstream gradient of frame i equal to
+ * scale[i] times its grad_normals buffer: the normal estimator as a loss layer
+ * without forming dL/dn_hat in a separate pass. For the cosine loss
+ * L = mean over valid pixels of (1 - n_hat . t), whose gradient is
+ * dL/dn_hat = -t / N_valid on valid pixels, pass the target normals t as
+ * grad_normals (float4, 4th component ignored) and scale[i] = -1 / N_valid(i).
+ * scale: a device array of n floats (4-byte aligned; NRM_ERR_INVALID_ARG if
+ * NULL), read by the kernel, so it may be computed on the GPU in the same
+ * stream. Otherwise exactly nrm_backward_batched (bit for bit equal to it on
+ * grad_normals = scale[i] * t rounded to float32). */
+NRM_API int nrm_backward_batched_scaled(nrm_handle* h, const nrm_grad_frame* frames, int n, const float* scale,
+                                        void* cuda_stream);
+
 /* Spherical angle images of a normal map (Section 4, the I_phi and I_theta
  * images, normalised to [0, 2 pi]): for each valid pixel
  *   phi = atan2(n_y, n_x) in [0, 2 pi),  theta = atan2(sqrt(n_x^2 + n_y^2), n_z) in [0, pi];

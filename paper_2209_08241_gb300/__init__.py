@@ -501,6 +501,27 @@ class BatchedEstimator(_Handle):
         _lib.check(self.lib.nrm_backward_batched(self.h, grad_frames_array, int(n), _stream_ptr(stream)),
                    "nrm_backward_batched")
 
+    def run_backward_scaled(self, grad_frames_array, n: int, scale: torch.Tensor, stream=None):
+        """``nrm_backward_batched_scaled``: the upstream gradient of frame i is
+        scale[i] times its grad_normals buffer (a float32 device tensor of n
+        values, e.g. -1 / N_valid with target normals for the cosine loss)."""
+        _check_dense(scale, (int(n),), torch.float32, self.device, "scale")
+        _lib.check(self.lib.nrm_backward_batched_scaled(self.h, grad_frames_array, int(n), scale.data_ptr(),
+                                                        _stream_ptr(stream)), "nrm_backward_batched_scaled")
+
+    def cosine_loss_backward(self, items: Sequence, targets: Sequence, valids: Sequence,
+                             grad_depths: Sequence | None = None, stream=None):
+        """Depth gradients of L_i = mean over the valid pixels of frame i of
+        (1 - n_hat . t) for each frame i of a batch, in one adjoint launch with
+        no dL/dn_hat buffer: targets [(H, W, 4) float32 unit normals, 4th
+        component ignored], valids the forward's masks. Returns the gradients
+        and the per-frame scale -1 / max(N_valid, 1) it used."""
+        arr, outs = self.make_grad_frames(items, targets, valids, grad_depths)
+        counts = torch.stack([v.sum(dtype=torch.float32) for v in valids]) if valids else torch.empty(0)
+        scale = (-1.0 / counts.clamp(min=1.0)).to(torch.float32).contiguous()
+        self.run_backward_scaled(arr, len(items), scale, stream)
+        return outs, scale
+
     def backward(self, items: Sequence, grad_normals: Sequence, valids: Sequence,
                  grad_depths: Sequence | None = None, stream=None) -> list:
         """Adjoint of a batch in one launch (see ``make_grad_frames``); returns

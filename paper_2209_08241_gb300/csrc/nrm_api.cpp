@@ -1172,8 +1172,24 @@ int nrm_backward(nrm_handle* h, const void* depth, const float* grad_normals, co
   return NRM_OK;
 }
 
+static int backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, const float* scale,
+                            void* cuda_stream);
+
 int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, void* cuda_stream) {
   g_last_error.clear();
+  return backward_batched(h, frames, n, nullptr, cuda_stream);
+}
+
+int nrm_backward_batched_scaled(nrm_handle* h, const nrm_grad_frame* frames, int n, const float* scale,
+                                void* cuda_stream) {
+  g_last_error.clear();
+  if (n > 0 && !scale) return fail(NRM_ERR_INVALID_ARG, "scale is NULL");
+  if ((uintptr_t)scale % 4) return fail(NRM_ERR_INVALID_ARG, "scale not 4-byte aligned");
+  return backward_batched(h, frames, n, scale, cuda_stream);
+}
+
+static int backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, const float* scale,
+                            void* cuda_stream) {
   if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
   if (n < 0) return fail(NRM_ERR_INVALID_ARG, "n < 0");
   if (n == 0) return NRM_OK;
@@ -1220,7 +1236,7 @@ int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, voi
       max_tiles = std::max(max_tiles, fdv[i].tiles_x * ((f.H + TY - 1) / TY));
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    NRM_CUDA(nrm::launch_backward_batched_param(fdv.data(), mapv.data(), n, max_tiles, make_globals(h), st),
+    NRM_CUDA(nrm::launch_backward_batched_param(fdv.data(), mapv.data(), n, max_tiles, make_globals(h), st, scale),
              "launch bwd_batched_param_kernel");
     NRM_CHECK(mark_single(h, st));
     return NRM_OK;
@@ -1272,7 +1288,7 @@ int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, voi
   nrm::Globals g = make_globals(h);
   int max_tiles = 0;
   for (int i = 0; i < n; ++i) max_tiles = std::max(max_tiles, fd[i].tiles_x * ((frames[i].H + TY - 1) / TY));
-  NRM_CUDA(nrm::launch_backward_batched(args, n, max_tiles, g, st), "launch bwd_batched_kernel");
+  NRM_CUDA(nrm::launch_backward_batched(args, n, max_tiles, g, st, scale), "launch bwd_batched_kernel");
   NRM_CUDA(cudaEventRecord(s.done, st), "cudaEventRecord");
   s.in_flight = true;
   return NRM_OK;

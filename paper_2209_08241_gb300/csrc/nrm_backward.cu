@@ -70,7 +70,10 @@ __host__ __device__ inline unsigned coord_table_bytes(int alpha) {
 template <int ALPHA>
 __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d, const void* tmap_g,
                                          const void* tmap_m, int gx0, int gy0, const Globals& g,
-                                         unsigned char* smem) {
+                                         unsigned char* smem, const float* __restrict__ scale, int frame) {
+  // Upstream gradient = scale[frame] x the staged float4 when scale is given
+  // (the fused loss entry: the staged values are then target normals).
+  const float sc = scale ? __ldg(scale + frame) : 1.0f;
   const int alpha = ALPHA > 0 ? ALPHA : g.alpha;
   const int p2 = pad_x(2 * alpha, 4);
   const int bw = TX + 2 * p2;       // depth tile pitch
@@ -162,7 +165,12 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d
       const float q = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
       const float inv = rsqrt_ftz(fmaxf(q, 1.17549435e-38f));
       const float hx0 = nx * inv, hy0 = ny * inv, hz0 = nz * inv;
-      const float4 gv = gw[i];
+      float4 gv = gw[i];
+      if (scale) {
+        gv.x *= sc;
+        gv.y *= sc;
+        gv.z *= sc;
+      }
       const float gd = fmaf(gv.x, hx0, fmaf(gv.y, hy0, gv.z * hz0));
       const float si = g.sign * inv;
       const float hx = fmaf(-gd, hx0, gv.x) * si;
@@ -203,15 +211,16 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d
 
 template <int ALPHA>
 __global__ void __launch_bounds__(NT)
-    bwd_kernel(const __grid_constant__ FrameDesc fd, const __grid_constant__ BwdMaps maps, const Globals g) {
+    bwd_kernel(const __grid_constant__ FrameDesc fd, const __grid_constant__ BwdMaps maps, const Globals g,
+               const float* scale) {
   extern __shared__ __align__(128) unsigned char smem[];
-  bwd_tile<ALPHA>(fd, &fd.tmap, &maps.grad, &maps.mask, blockIdx.x * TX, blockIdx.y * TY, g, smem);
+  bwd_tile<ALPHA>(fd, &fd.tmap, &maps.grad, &maps.mask, blockIdx.x * TX, blockIdx.y * TY, g, smem, scale, 0);
 }
 
 // Grid (max tiles of a frame, frames): block (x, f) is tile x of frame f; frames
 // with fewer tiles leave their extra blocks idle.
 template <int ALPHA>
-__global__ void __launch_bounds__(NT) bwd_batched_kernel(const BwdBatchArgs args, const Globals g) {
+__global__ void __launch_bounds__(NT) bwd_batched_kernel(const BwdBatchArgs args, const Globals g, const float* scale) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int f = (int)blockIdx.y;
   const FrameDesc& fd = args.frames[f];
@@ -225,7 +234,7 @@ __global__ void __launch_bounds__(NT) bwd_batched_kernel(const BwdBatchArgs args
   }
   const int ty = local / tiles_x;
   const int tx = local - ty * tiles_x;
-  bwd_tile<ALPHA>(fd, &fd.tmap, &args.maps[f].grad, &args.maps[f].mask, tx * TX, ty * TY, g, smem);
+  bwd_tile<ALPHA>(fd, &fd.tmap, &args.maps[f].grad, &args.maps[f].mask, tx * TX, ty * TY, g, smem, scale, f);
 }
 
 // A batch of at most kBwdParamMaxFrames frames with its records and tensor
@@ -240,7 +249,7 @@ static_assert(sizeof(BwdParamBatch) <= 32764, "the descriptor block must fit the
 // Grid (max tiles of a frame, frames), as bwd_batched_kernel.
 template <int ALPHA>
 __global__ void __launch_bounds__(NT)
-    bwd_batched_param_kernel(const __grid_constant__ BwdParamBatch pb, const Globals g) {
+    bwd_batched_param_kernel(const __grid_constant__ BwdParamBatch pb, const Globals g, const float* scale) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int f = (int)blockIdx.y;
   const FrameDesc& fd = pb.frames[f];
@@ -249,7 +258,7 @@ __global__ void __launch_bounds__(NT)
   if (tiles_x == 0 || local >= tiles_x * ((fd.H + TY - 1) / TY)) return;
   const int ty = local / tiles_x;
   const int tx = local - ty * tiles_x;
-  bwd_tile<ALPHA>(fd, &fd.tmap, &pb.maps[f].grad, &pb.maps[f].mask, tx * TX, ty * TY, g, smem);
+  bwd_tile<ALPHA>(fd, &fd.tmap, &pb.maps[f].grad, &pb.maps[f].mask, tx * TX, ty * TY, g, smem, scale, f);
 }
 
 const void* bwd_param_kernel_for(int alpha) {
@@ -296,7 +305,8 @@ unsigned bwd_smem_bytes(int alpha) {
   return depth_tile_bytes(alpha) + weight_tile_bytes(alpha) + mask_tile_bytes(alpha) + coord_table_bytes(alpha) + 16;
 }
 
-cudaError_t launch_backward(const FrameDesc& fd, const BwdMaps& maps, const Globals& g, cudaStream_t stream) {
+cudaError_t launch_backward(const FrameDesc& fd, const BwdMaps& maps, const Globals& g, cudaStream_t stream,
+                            const float* scale) {
   const unsigned smem = bwd_smem_bytes(g.alpha);
   const void* fn = bwd_kernel_for(g.alpha, false);
   cudaError_t e = set_smem(fn, smem);
@@ -305,26 +315,28 @@ cudaError_t launch_backward(const FrameDesc& fd, const BwdMaps& maps, const Glob
   FrameDesc d = fd;
   BwdMaps m = maps;
   Globals gg = g;
-  void* args[3] = {&d, &m, &gg};
+  const float* sc = scale;
+  void* args[4] = {&d, &m, &gg, &sc};
   e = cudaLaunchKernel(fn, grid, dim3(NT), args, smem, stream);
   return e;
 }
 
 cudaError_t launch_backward_batched(const BwdBatchArgs& args, int n_frames, int max_tiles, const Globals& g,
-                                    cudaStream_t stream) {
+                                    cudaStream_t stream, const float* scale) {
   const unsigned smem = bwd_smem_bytes(g.alpha);
   const void* fn = bwd_kernel_for(g.alpha, true);
   cudaError_t e = set_smem(fn, smem);
   if (e != cudaSuccess) return e;
   BwdBatchArgs a = args;
   Globals gg = g;
-  void* kargs[2] = {&a, &gg};
+  const float* sc = scale;
+  void* kargs[3] = {&a, &gg, &sc};
   e = cudaLaunchKernel(fn, dim3(max_tiles, n_frames), dim3(NT), kargs, smem, stream);
   return e;
 }
 
 cudaError_t launch_backward_batched_param(const FrameDesc* frames, const BwdMaps* maps, int n_frames, int max_tiles,
-                                          const Globals& g, cudaStream_t stream) {
+                                          const Globals& g, cudaStream_t stream, const float* scale) {
   if (n_frames < 1 || n_frames > kBwdParamMaxFrames) return cudaErrorInvalidValue;
   const unsigned smem = bwd_smem_bytes(g.alpha);
   const void* fn = bwd_param_kernel_for(g.alpha);
@@ -337,7 +349,8 @@ cudaError_t launch_backward_batched_param(const FrameDesc* frames, const BwdMaps
   std::memcpy(pb->frames, frames, sizeof(FrameDesc) * (size_t)n_frames);
   std::memcpy(pb->maps, maps, sizeof(BwdMaps) * (size_t)n_frames);
   Globals gg = g;
-  void* kargs[2] = {pb, &gg};
+  const float* sc = scale;
+  void* kargs[3] = {pb, &gg, &sc};
   return cudaLaunchKernel(fn, dim3(max_tiles, n_frames), dim3(NT), kargs, smem, stream);
 }
 

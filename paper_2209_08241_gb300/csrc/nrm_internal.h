@@ -185,16 +185,19 @@ unsigned bwd_smem_bytes(int alpha);
 // fd.tmap maps the depth with box (kBwdTileX + 2 pad_x(2 alpha, 4)) x (kBwdTileY + 4 alpha);
 // fd.normals holds the upstream gradient, fd.valid the mask, fd.grad_depth the output.
 // fd.use_tma = 1 only if all three maps (fd.tmap, maps.grad, maps.mask) are valid.
-cudaError_t launch_backward(const FrameDesc& fd, const BwdMaps& maps, const Globals& g, cudaStream_t stream);
+// scale (optional, device array indexed by frame): the upstream gradient is
+// scale[frame] times the float4 buffer (then a target normal map).
+cudaError_t launch_backward(const FrameDesc& fd, const BwdMaps& maps, const Globals& g, cudaStream_t stream,
+                            const float* scale = nullptr);
 // All tiles of a batch in one launch (grid max_tiles x n_frames); the descriptor
 // block is in device memory.
 cudaError_t launch_backward_batched(const BwdBatchArgs& args, int n_frames, int max_tiles, const Globals& g,
-                                    cudaStream_t stream);
+                                    cudaStream_t stream, const float* scale = nullptr);
 // The same for at most kBwdParamMaxFrames frames with the records and maps
 // (host arrays) passed as one kernel parameter: no upload, no fences.
 constexpr int kBwdParamMaxFrames = 60;
 cudaError_t launch_backward_batched_param(const FrameDesc* frames, const BwdMaps* maps, int n_frames, int max_tiles,
-                                          const Globals& g, cudaStream_t stream);
+                                          const Globals& g, cudaStream_t stream, const float* scale = nullptr);
 
 // Evaluation kernels (nrm_eval.cu).
 constexpr int kMseBlocks = 2048;  // fixed, so that the reduction order never changes

@@ -176,3 +176,67 @@ def test_batch_autograd_matches_per_frame_autograd():
         total = total + (1.0 - (ni[..., :3] * t[i]).sum(-1))[mi.bool()].sum()
     (total / nv).backward()
     torch.testing.assert_close(x.grad, y.grad, rtol=1e-5, atol=1e-6 * y.grad.abs().max().item())
+
+
+def test_scaled_adjoint_equals_adjoint_of_scaled_gradient():
+    """nrm_backward_batched_scaled(t, s) is nrm_backward_batched(s * t) bit for
+    bit (the kernel forms the same float32 product), for a parameter-block
+    batch and a descriptor-ring batch (70 frames), with per-frame scales."""
+    b = nrm.BatchedEstimator(nrm.NormalParams())
+    for nfr in (3, 70):
+        items = [frame(30 + i, W, H) for i, (W, H) in enumerate([(160, 120), (97, 61), (640, 480)] * 24)][:nfr]
+        outs = b(items)
+        ts = [scenes.unit_targets(1, d.shape[0], d.shape[1], seed=40 + i, device=DEV)[0] for i, (d, _) in enumerate(items)]
+        t4 = []
+        for t in ts:
+            x = torch.zeros((*t.shape[:2], 4), device=DEV)
+            x[..., :3] = t
+            t4.append(x)
+        scale = (-1.0 / torch.arange(1, nfr + 1, device=DEV, dtype=torch.float32) * 0.37).contiguous()
+        arr, got = b.make_grad_frames(items, t4, [m for _, m in outs])
+        b.run_backward_scaled(arr, nfr, scale)
+        g4 = [t * scale[i] for i, t in enumerate(t4)]
+        ref = b.backward(items, g4, [m for _, m in outs])
+        torch.cuda.synchronize()
+        for a, r in zip(got, ref):
+            assert torch.equal(a, r)
+    b.sync_status()
+
+
+def test_cosine_loss_backward_matches_complex_step_oracle():
+    """The fused loss entry against the oracle's VJP of L = mean over valid
+    pixels of (1 - n_hat . t), per frame, on crops of two frames."""
+    b = nrm.BatchedEstimator(nrm.NormalParams())
+    items = [frame(50 + i) for i in range(2)]
+    outs = b(items)
+    t4 = []
+    for i, (d, _) in enumerate(items):
+        t = scenes.unit_targets(1, d.shape[0], d.shape[1], seed=60 + i, device=DEV)[0]
+        x = torch.zeros((t.shape[0], t.shape[1], 4), device=DEV)
+        x[..., :3] = t
+        t4.append(x)
+    grads, scale = b.cosine_loss_backward(items, t4, [m for _, m in outs])
+    torch.cuda.synchronize()
+    b.sync_status()
+    for i, ((d, K), (n, m)) in enumerate(zip(items, outs)):
+        assert float(scale[i]) == pytest.approx(-1.0 / float(m.sum()), rel=1e-6)
+        gn = (t4[i][..., :3].double() * (-1.0 / float(m.sum())) * m[..., None].double()).cpu().numpy()
+        for (y0, x0) in ((0, 0), (210, 290)):
+            ref = oracle.vjp(d.cpu().numpy(), K, gn, m.cpu().numpy(), alpha=2, crop=(y0, x0, 64, 64), nthreads=NT)
+            got = grads[i][y0:y0 + 64, x0:x0 + 64].double().cpu().numpy()
+            sc = np.abs(ref).max()
+            big = np.abs(ref) > 1e-3 * sc
+            rel = np.abs(got - ref)[big] / np.abs(ref)[big]
+            assert rel.max() <= 1e-3, (i, y0, x0, rel.max())
+            assert np.abs(got - ref)[~big].max(initial=0) <= 1e-3 * sc
+
+
+def test_scaled_adjoint_rejects_missing_scale():
+    from paper_2209_08241_gb300 import _lib
+    b = nrm.BatchedEstimator(nrm.NormalParams())
+    items = [frame(70, 64, 48)]
+    outs = b(items)
+    arr, _ = b.make_grad_frames(items, [torch.zeros((48, 64, 4), device=DEV)], [outs[0][1]])
+    rc = b.lib.nrm_backward_batched_scaled(b.h, arr, 1, None, None)
+    assert rc == _lib.NRM_ERR_INVALID_ARG
+    b.sync_status()
