@@ -5,18 +5,23 @@ intrinsics) arrive in host memory. The server
 
   * admits a waiting request when a device buffer set for its frame size is
     free or can be created within the device-memory budget (buffers stay
-    resident and are reused by later requests of the same size);
+    resident and are reused by later requests of the same size), and, when it
+    delivers results, a pinned host buffer set for them within the host budget;
   * copies the admitted frames to the device and launches everything admitted
     so far as ONE batched persistent launch (``nrm_estimate_batched``) on the
-    next free stream, so a batch starts while earlier batches are still on the
-    GPU and their work overlaps;
-  * retires batches as their completion events fire, hands each finished
-    request to the ``on_done`` callback (results are views of the resident
-    buffers, valid until the callback returns) and frees the buffers.
+    next free stream, followed by the copies of every result (normals and
+    mask) back to the request's pinned host buffers, so a batch's uploads,
+    kernel and downloads overlap those of the batches before and after it;
+  * retires batches as their completion events fire (after the downloads), and
+    hands each finished request to the ``on_done`` callback with its results
+    in host memory (``Request.normals`` / ``Request.valid``, valid until the
+    callback returns; copy them to keep them) before recycling the buffers.
 
 Per-request latency is completion time minus arrival time, both on the host
-clock. ``PlainServer`` is the baseline: one plain per-frame launch per request,
-in arrival order, on one stream.
+clock, so it includes the result's delivery to host memory. ``PlainServer``
+is the baseline: one plain per-frame launch per request, in arrival order, on
+one stream, with the same upload and delivery. With ``deliver=False`` results
+stay on the device (``Request.buffers`` during the callback).
 
 All normal arithmetic runs in the library's CUDA kernels; this module only
 schedules, copies and keeps books.
@@ -48,7 +53,10 @@ class Request:
     t_arrival: float = 0.0       # host clock (time.perf_counter)
     t_launch: float = 0.0
     t_done: float = 0.0
-    buffers: Optional["BufferSet"] = None
+    buffers: Optional["BufferSet"] = None       # device buffers while on the GPU
+    host: Optional["BufferSet"] = None          # pinned result buffers while delivering
+    normals: Optional[torch.Tensor] = None      # delivered results (host), during on_done
+    valid: Optional[torch.Tensor] = None
 
     @property
     def latency(self) -> float:
@@ -70,35 +78,39 @@ class BufferSet:
 
 
 class BufferPool:
-    """Device buffer sets per (H, W, depth dtype), bounded by a byte budget.
+    """Buffer sets per (H, W, depth dtype), bounded by a byte budget: device
+    sets (depth, normals, mask) or, with ``host=True``, pinned host sets for
+    delivered results (normals, mask; the depth field is an empty tensor).
 
     acquire() returns a free set of the right size, or creates one if the
     budget allows, else None (the request waits). Free sets of other sizes are
     evicted (their memory returned to the allocator) when that makes room."""
 
-    def __init__(self, budget_bytes: int, out_dtype: torch.dtype, device):
+    def __init__(self, budget_bytes: int, out_dtype: torch.dtype, device, host: bool = False):
         self.budget = int(budget_bytes)
         self.out_dtype = out_dtype
         self.device = device
+        self.host = bool(host)
         self.free: dict = collections.defaultdict(list)
         self.reserved = 0   # bytes of all sets, free or in use
         self.in_use = 0
 
     @staticmethod
-    def set_bytes(H: int, W: int, depth_dtype: torch.dtype, out_dtype: torch.dtype) -> int:
-        """Device bytes of one buffer set: depth, normals and mask of an H x W frame."""
-        eb = 2 if depth_dtype == torch.uint16 else 4
+    def set_bytes(H: int, W: int, depth_dtype: torch.dtype, out_dtype: torch.dtype, host: bool = False) -> int:
+        """Bytes of one buffer set of an H x W frame: depth (device sets only),
+        normals and mask."""
+        eb = 0 if host else (2 if depth_dtype == torch.uint16 else 4)
         ob = {torch.float32: 16, torch.float16: 8, torch.int16: 4}[out_dtype]
         return H * W * (eb + ob + 1)
 
     def acquire(self, H: int, W: int, depth_dtype: torch.dtype) -> Optional[BufferSet]:
         """A free buffer set for this frame size, a new one within the budget, or None."""
-        key = (H, W, depth_dtype)
+        key = (H, W, None if self.host else depth_dtype)  # host sets hold no depth
         if self.free[key]:
             b = self.free[key].pop()
             self.in_use += b.nbytes
             return b
-        need = self.set_bytes(H, W, depth_dtype, self.out_dtype)
+        need = self.set_bytes(H, W, depth_dtype, self.out_dtype, self.host)
         if need > self.budget:
             raise ValueError(f"a {H}x{W} frame needs {need} bytes, more than the whole budget")
         # Evict free sets of other sizes until the new one fits.
@@ -110,11 +122,16 @@ class BufferPool:
             self.reserved -= b.nbytes
             del b
         channels = 2 if self.out_dtype == torch.int16 else 4
-        b = BufferSet(key,
-                      torch.empty((H, W), dtype=depth_dtype, device=self.device),
-                      torch.empty((H, W, channels), dtype=self.out_dtype, device=self.device),
-                      torch.empty((H, W), dtype=torch.uint8, device=self.device),
-                      need)
+        if self.host:
+            b = BufferSet(key, torch.empty(0, dtype=depth_dtype),
+                          torch.empty((H, W, channels), dtype=self.out_dtype, pin_memory=True),
+                          torch.empty((H, W), dtype=torch.uint8, pin_memory=True), need)
+        else:
+            b = BufferSet(key,
+                          torch.empty((H, W), dtype=depth_dtype, device=self.device),
+                          torch.empty((H, W, channels), dtype=self.out_dtype, device=self.device),
+                          torch.empty((H, W), dtype=torch.uint8, device=self.device),
+                          need)
         self.reserved += need
         self.in_use += need
         return b
@@ -138,10 +155,13 @@ class NormalServer:
 
     def __init__(self, params: NormalParams | None = None, budget_bytes: int = 40 << 30,
                  streams: int = 3, max_batch: int = 256, device=None,
-                 on_done: Callable[[Request], None] | None = None):
+                 on_done: Callable[[Request], None] | None = None, deliver: bool = True,
+                 host_budget_bytes: int = 8 << 30):
         self.params = params or NormalParams()
         self.device = _device(device)
         self.pool = BufferPool(budget_bytes, self.params.torch_out_dtype, self.device)
+        self.deliver = bool(deliver)
+        self.host_pool = BufferPool(host_budget_bytes, self.params.torch_out_dtype, None, host=True)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(streams)]
         self.handles = [BatchedEstimator(self.params, device=self.device) for _ in range(streams)]
         self.free_streams = list(range(streams))
@@ -167,11 +187,7 @@ class NormalServer:
             b = self.inflight.popleft()
             now = time.perf_counter() if now is None else now
             for r in b.requests:
-                r.t_done = now
-                if self.on_done is not None:
-                    self.on_done(r)
-                self.pool.release(r.buffers)
-                r.buffers = None
+                _finish(r, now, self.on_done, self.pool, self.host_pool)
                 self.completed += 1
             self.free_streams.append(b.stream_index)
 
@@ -181,12 +197,9 @@ class NormalServer:
         batch = []
         while self.waiting and len(batch) < self.max_batch:
             r = self.waiting[0]
-            H, W = r.depth.shape
-            buf = self.pool.acquire(H, W, r.depth.dtype)
-            if buf is None:
+            if not _admit(r, self.pool, self.host_pool if self.deliver else None):
                 break
             self.waiting.popleft()
-            r.buffers = buf
             batch.append(r)
         if not batch:
             return
@@ -210,6 +223,10 @@ class NormalServer:
                 f.in_dtype = _lib.NRM_IN_U16_MM if b.depth.dtype == torch.uint16 else _lib.NRM_IN_F32_M
                 r.t_launch = t
             self.handles[si].run(arr, len(batch), stream)
+            if self.deliver:
+                for r in batch:
+                    r.host.normals.copy_(r.buffers.normals, non_blocking=True)
+                    r.host.valid.copy_(r.buffers.valid, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(stream)
         self.inflight.append(_Batch(ev, batch, si))
@@ -231,15 +248,49 @@ class NormalServer:
             h.sync_status()
 
 
+def _admit(r: Request, pool: BufferPool, host_pool: Optional[BufferPool]) -> bool:
+    """Device (and, when delivering, pinned host) buffers for r, or False."""
+    H, W = r.depth.shape
+    buf = pool.acquire(H, W, r.depth.dtype)
+    if buf is None:
+        return False
+    if host_pool is not None:
+        hb = host_pool.acquire(H, W, r.depth.dtype)
+        if hb is None:
+            pool.release(buf)
+            return False
+        r.host = hb
+    r.buffers = buf
+    return True
+
+
+def _finish(r: Request, now: float, on_done, pool: BufferPool, host_pool: BufferPool):
+    """Completes r at host time now: results to the callback, buffers back."""
+    r.t_done = now
+    if r.host is not None:
+        r.normals, r.valid = r.host.normals, r.host.valid
+    if on_done is not None:
+        on_done(r)
+    pool.release(r.buffers)
+    r.buffers = None
+    if r.host is not None:
+        host_pool.release(r.host)
+        r.host = None
+        r.normals = r.valid = None
+
+
 class PlainServer:
     """Baseline: one plain per-frame launch per request, in arrival order, on
-    one stream, with the same resident-buffer pool."""
+    one stream, with the same resident-buffer pools and result delivery."""
 
     def __init__(self, params: NormalParams | None = None, budget_bytes: int = 40 << 30, device=None,
-                 on_done: Callable[[Request], None] | None = None):
+                 on_done: Callable[[Request], None] | None = None, deliver: bool = True,
+                 host_budget_bytes: int = 8 << 30):
         self.params = params or NormalParams()
         self.device = _device(device)
         self.pool = BufferPool(budget_bytes, self.params.torch_out_dtype, self.device)
+        self.deliver = bool(deliver)
+        self.host_pool = BufferPool(host_budget_bytes, self.params.torch_out_dtype, None, host=True)
         self.stream = torch.cuda.Stream(self.device)
         self.estimators: collections.OrderedDict = collections.OrderedDict()
         self.waiting: collections.deque = collections.deque()
@@ -269,24 +320,21 @@ class PlainServer:
         while self.inflight and self.inflight[0][0].query():
             ev, r = self.inflight.popleft()
             now = time.perf_counter() if now is None else now
-            r.t_done = now
-            if self.on_done is not None:
-                self.on_done(r)
-            self.pool.release(r.buffers)
-            r.buffers = None
+            _finish(r, now, self.on_done, self.pool, self.host_pool)
             self.completed += 1
         while self.waiting:
             r = self.waiting[0]
-            H, W = r.depth.shape
-            buf = self.pool.acquire(H, W, r.depth.dtype)
-            if buf is None:
+            if not _admit(r, self.pool, self.host_pool if self.deliver else None):
                 break
             self.waiting.popleft()
-            r.buffers = buf
+            buf = r.buffers
             r.t_launch = time.perf_counter()
             with torch.cuda.stream(self.stream):
                 buf.depth.copy_(r.depth, non_blocking=True)
                 self._estimator(r).estimate(buf.depth, buf.normals, buf.valid, self.stream)
+                if self.deliver:
+                    r.host.normals.copy_(buf.normals, non_blocking=True)
+                    r.host.valid.copy_(buf.valid, non_blocking=True)
                 ev = torch.cuda.Event()
                 ev.record(self.stream)
             self.inflight.append((ev, r))

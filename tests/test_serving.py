@@ -43,6 +43,8 @@ def test_pool_reuses_and_respects_budget():
 def test_pool_set_bytes():
     assert BufferPool.set_bytes(2, 3, torch.uint16, torch.float32) == 6 * (2 + 16 + 1)
     assert BufferPool.set_bytes(2, 3, torch.float32, torch.float16) == 6 * (4 + 8 + 1)
+    # Host sets hold the delivered results only (normals and mask).
+    assert BufferPool.set_bytes(2, 3, torch.uint16, torch.float32, host=True) == 6 * (16 + 1)
 
 
 def _requests(n, seed=0):
@@ -58,8 +60,13 @@ def _requests(n, seed=0):
 
 
 def _collect(store):
+    """Keeps each request's results as delivered to host memory, after checking
+    that they are the device results."""
     def on_done(r):
-        store[r.rid] = (r.buffers.normals.clone(), r.buffers.valid.clone())
+        assert r.normals is not None and r.normals.device.type == "cpu" and r.normals.is_pinned()
+        n, v = r.normals.clone(), r.valid.clone()
+        assert torch.equal(n, r.buffers.normals.cpu()) and torch.equal(v, r.buffers.valid.cpu())
+        store[r.rid] = (n, v)
     return on_done
 
 
@@ -132,3 +139,27 @@ def test_plain_baseline_agrees_with_batched_server():
     base.sync_status()
     for r in reqs:
         assert torch.equal(a[r.rid][0], b[r.rid][0]) and torch.equal(a[r.rid][1], b[r.rid][1])
+
+
+@pytest.mark.gpu
+def test_results_stay_on_the_device_without_delivery():
+    reqs = _requests(4, seed=3)
+    got = {}
+
+    def on_done(r):
+        assert r.normals is None and r.host is None
+        got[r.rid] = (r.buffers.normals.clone(), r.buffers.valid.clone())
+
+    srv = NormalServer(on_done=on_done, deliver=False)
+    for r in reqs:
+        srv.submit(Request(r.rid, r.depth, r.K))
+    srv.drain()
+    srv.sync_status()
+    ref = {}
+    srv2 = NormalServer(on_done=_collect(ref))
+    for r in reqs:
+        srv2.submit(Request(r.rid, r.depth, r.K))
+    srv2.drain()
+    for r in reqs:
+        assert torch.equal(got[r.rid][0].cpu(), ref[r.rid][0]) and torch.equal(got[r.rid][1].cpu(), ref[r.rid][1])
+    assert srv2.host_pool.in_use == 0 and srv2.pool.in_use == 0
