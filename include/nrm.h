@@ -28,6 +28,15 @@
  *     and mask byte 0; valid pixels get mask byte 1.
  *   - Sign: the paper's normal points away from the camera (n . P1 > 0);
  *     orient_to_camera = 1 negates it.
+ *   - Numerical domain: the kernels evaluate Eq. 4-6 and the statistic in
+ *     FP32. For depths d (metres, after depth_scale) with
+ *     2^-28 <= alpha d / f <= 2^28 for f = fx and fy (at f = 525 px and
+ *     alpha = 2: about 1e-6 m to 7e10 m) no product under- or overflows, the
+ *     normal is within 1e-6 rad of the FP64 definition and the mask decides
+ *     like it except where the statistic lies within 1e-6 relative of tau
+ *     (tested at both ends). Below that range q = n . n falls under FLT_MIN
+ *     and pixels are reported invalid; above it the statistic overflows and
+ *     results are unspecified.
  *
  * Memory and ownership: every depth, normal, mask and gradient pointer passed
  * to this library is a DEVICE pointer owned by the caller (except in

@@ -207,13 +207,20 @@ def ms_kappa(depth, K, alphas, form, depth_scale=0.001):
         return np.where(den > 0, mag / den, np.inf)
 
 
+# The widened band may exclude at most this fraction of a frame's pixels
+# beyond those the plain 1e-6 band excludes (kappa is large only where the
+# per-scale normals nearly cancel, which is rare on real surfaces).
+MS_KAPPA_EXCLUDED_FRAC = 1e-4
+
+
 def compare_ms(normals, valid, ref, tau, kappa, half=False, what=""):
     """Multi-scale output against the multi-scale oracle. As ``compare``, but a
     pixel is excluded from the mask comparison when its statistic is within
     1e-6 kappa relative of tau: the FP32 sums over scales carry relative errors
     of a few ulp of the per-scale magnitudes, i.e. kappa times more relative to
-    the average. Returns (near_tau_count, max_angle, n_valid, max kappa over
-    the compared pixels)."""
+    the average. The pixels excluded only because of the widening are counted
+    and bounded by MS_KAPPA_EXCLUDED_FRAC of the frame. Returns
+    (near_tau_count, max_angle, n_valid, max kappa over the compared pixels)."""
     if isinstance(normals, torch.Tensor):
         normals = normals.detach().float().cpu().numpy()
     if isinstance(valid, torch.Tensor):
@@ -224,6 +231,10 @@ def compare_ms(normals, valid, ref, tau, kappa, half=False, what=""):
     band = NEAR_TAU_REL * np.maximum(1.0, np.nan_to_num(kappa, nan=1.0, posinf=1e30))
     with np.errstate(invalid="ignore"):
         near = np.isfinite(ref.stat) & (np.abs(ref.stat - tau) <= band * tau)
+        near_plain = np.isfinite(ref.stat) & (np.abs(ref.stat - tau) <= NEAR_TAU_REL * tau)
+    widened_only = int((near & ~near_plain).sum())
+    assert widened_only <= MS_KAPPA_EXCLUDED_FRAC * m.size, (
+        f"{what}: the kappa-widened band excluded {widened_only} pixels (> {MS_KAPPA_EXCLUDED_FRAC} of {m.size})")
     mism = (m != ref.valid) & ~near
     assert mism.sum() == 0, (f"{what}: {int(mism.sum())} mask mismatches, e.g. at "
                              f"{np.argwhere(mism)[:5].tolist()}")

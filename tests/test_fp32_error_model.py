@@ -118,3 +118,17 @@ def test_grazing_planes(tilt_deg, alpha):
     raw = np.clip(np.round(z * 1000.0), 0, 65535).astype(np.uint16)
     raw[(z < 0.4) | (z > 6.0)] = 0
     check(raw, K, alpha)
+
+
+@pytest.mark.parametrize("k", [2.0 ** -18, 2.0 ** 33])
+@pytest.mark.parametrize("alpha", [1, 2])
+def test_numerical_domain_ends(k, alpha):
+    """The documented FP32 domain, 2^-28 <= alpha d / f <= 2^28: a float32 scene
+    (0.4 .. 6 m, f = 525 px) scaled by k to depths of about 1.5e-6 .. 2.3e-5 m
+    and 3.4e9 .. 5.2e10 m still meets both claims."""
+    d, K = scenes.random_frame(91, 640, 480, "cpu", kind="f32")
+    dd = (d.numpy().astype(np.float64) * k).astype(f32)
+    valid = dd[dd > 0]
+    f = min(K[0], K[1])
+    assert alpha * valid.min() / f >= 2.0 ** -28 and alpha * valid.max() / f <= 2.0 ** 28
+    check(dd, K, alpha)

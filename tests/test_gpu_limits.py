@@ -119,3 +119,21 @@ def test_plane_fit_rejects_too_many_tile_rows():
     with pytest.raises(nrm._lib.NrmError):
         est.plane_fit(d, 1)
     est.sync_status()
+
+
+@pytest.mark.parametrize("k", [2.0 ** -18, 2.0 ** 33])
+def test_numerical_domain_ends_match_oracle(k):
+    """Depths at both ends of the documented FP32 domain (2^-28 <= alpha d / f
+    <= 2^28): a float32 scene scaled to about 1.5e-6 .. 2.3e-5 m and to
+    3.4e9 .. 5.2e10 m against the FP64 oracle, for alpha = 1 and 2."""
+    from synth import scenes
+    d0, K = scenes.random_frame(91, 640, 480, "cpu", kind="f32")
+    d = (d0.double() * k).float()
+    for alpha in (1, 2):
+        p = nrm.NormalParams(alpha=alpha)
+        est = nrm.NormalEstimator(K, 480, 640, p)
+        n, m = est(d.cuda())
+        est.sync_status()
+        ref = oracle.forward(d.numpy(), K, alpha=alpha, stat_mode=oracle.STAT_SECANT, tau=p.tau, nthreads=8)
+        near, ang, nv = compare(n, m, ref, p.tau, what=f"k={k} alpha={alpha}")
+        assert nv > 100000
