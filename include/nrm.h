@@ -79,7 +79,8 @@ typedef enum {
   NRM_ERR_CUDA = 3,        /* a CUDA runtime call failed (see nrm_last_error) */
   NRM_ERR_OOM = 4,         /* a device or pinned allocation failed */
   NRM_ERR_TIMEOUT = 5,     /* a bounded device wait ran out */
-  NRM_ERR_NO_DEVICE = 6    /* no CUDA device is visible */
+  NRM_ERR_NO_DEVICE = 6,   /* no CUDA device is visible */
+  NRM_ERR_BOUNDS = 7       /* checking build only: an index left its buffer (the access was skipped) */
 } nrm_status;
 
 /* Pinhole intrinsics in pixels (Section 2: f_x, f_y, o_x, o_y); fx, fy > 0. */
@@ -326,6 +327,16 @@ NRM_API int nrm_plane_fit(nrm_handle* h, const void* depth, float* normals, uint
  * timeout (*elapsed_ms, if not NULL, gets the kernel's duration), or
  * NRM_ERR_CUDA. Leaves the context usable; allocates and frees 8 bytes. */
 NRM_API int nrm_selftest_wait_expiry(unsigned long long timeout_ns, float* elapsed_ms);
+
+/* Self-test of the range checks of the checking build (build.py --debug; no
+ * counterpart in the paper). Evaluates the checks on addresses inside and
+ * just outside a shared-memory block, a global array and an index range,
+ * forming and comparing addresses only (nothing outside a buffer is touched),
+ * and writes results[0..6] (1 = accepted, 0 = rejected; right is
+ * 1, 1, 0, 0, 1, 0, 0) and results[7] = the status word (NRM_ERR_BOUNDS after
+ * the rejections). Synchronous; allocates and frees 36 bytes. Returns
+ * NRM_ERR_UNSUPPORTED in the ordinary build. */
+NRM_API int nrm_selftest_bounds(int* results);
 
 /* Waits for the handle's work, returns the device status word (NRM_OK or the
  * first device-side error since the last call) and clears it. */

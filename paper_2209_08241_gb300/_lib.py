@@ -7,6 +7,7 @@ be built or loaded, ``load()`` raises.
 from __future__ import annotations
 
 import ctypes
+import os
 import threading
 
 from . import build as _build
@@ -18,6 +19,7 @@ NRM_ERR_CUDA = 3
 NRM_ERR_OOM = 4
 NRM_ERR_TIMEOUT = 5
 NRM_ERR_NO_DEVICE = 6
+NRM_ERR_BOUNDS = 7
 
 NRM_IN_F32_M, NRM_IN_U16_MM = 0, 1
 NRM_OUT_F32X4, NRM_OUT_F16X4, NRM_OUT_OCT16 = 0, 1, 2
@@ -99,6 +101,7 @@ SIGNATURES = [
                                                        ctypes.POINTER(Scales), _S]),
     ("nrm_plane_fit", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _S]),
     ("nrm_selftest_wait_expiry", ctypes.c_int, [ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_float)]),
+    ("nrm_selftest_bounds", ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
     ("nrm_sync_status", ctypes.c_int, [_H]),
     ("nrm_get_config", ctypes.c_int, [_H, ctypes.POINTER(TileConfig)]),
     ("nrm_set_config", ctypes.c_int, [_H, ctypes.POINTER(TileConfig)]),
@@ -129,7 +132,7 @@ class NrmError(RuntimeError):
 
 def status_name(code: int) -> str:
     names = {0: "NRM_OK", 1: "NRM_ERR_INVALID_ARG", 2: "NRM_ERR_UNSUPPORTED", 3: "NRM_ERR_CUDA",
-             4: "NRM_ERR_OOM", 5: "NRM_ERR_TIMEOUT", 6: "NRM_ERR_NO_DEVICE"}
+             4: "NRM_ERR_OOM", 5: "NRM_ERR_TIMEOUT", 6: "NRM_ERR_NO_DEVICE", 7: "NRM_ERR_BOUNDS"}
     return names.get(code, f"status {code}")
 
 
@@ -138,7 +141,8 @@ def load():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            # NRM_LIB_VARIANT=debug selects the range-checking build.
+            path = _build.build(debug=os.environ.get("NRM_LIB_VARIANT", "") == "debug")
             lib = ctypes.CDLL(path)
             for name, res, args in SIGNATURES:
                 fn = getattr(lib, name)

@@ -6,7 +6,14 @@ with the CUDA runtime linked statically (so it loads on machines without a
 GPU, where its calls return NRM_ERR_NO_DEVICE), and writes it to
 ``_build/libnrm.so``. No torch types cross this library's interface.
 
-Usage: ``python -m paper_2209_08241_gb300.build [--force] [--verbose]``.
+With ``debug=True`` (``--debug``) it builds the checking variant
+``_build/libnrm_debug.so`` instead (``-DNRM_DEBUG_CHECKS``: every shared-memory
+access and every geometry-dependent global access of the kernels is
+range-checked; a failed check skips the access, prints the site and records
+NRM_ERR_BOUNDS in the status word). The binding loads it when the environment
+variable NRM_LIB_VARIANT is ``debug``.
+
+Usage: ``python -m paper_2209_08241_gb300.build [--force] [--verbose] [--debug]``.
 """
 from __future__ import annotations
 
@@ -22,6 +29,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnrm.so")
+DEBUG_BUILD = os.path.join(BUILD, "debug")
+DEBUG_LIB = os.path.join(BUILD, "libnrm_debug.so")
 
 SOURCES = ["nrm_forward.cu", "nrm_forward_points.cu", "nrm_forward_param.cu", "nrm_backward.cu", "nrm_api.cpp", "nrm_noalloc.cu", "nrm_eval.cu", "nrm_planefit.cu", "nrm_multiscale.cu", "nrm_selftest.cu"]
 HEADERS = ["nrm_internal.h", "nrm_device.cuh", "nrm_forward_kernels.cuh"]
@@ -42,16 +51,19 @@ def _inputs():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(debug: bool = False) -> bool:
+    lib = DEBUG_LIB if debug else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def _compile(nvcc: str, src: str, obj: str, verbose: bool) -> None:
+def _compile(nvcc: str, src: str, obj: str, verbose: bool, debug: bool = False) -> None:
     cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
            f"-I{INCLUDE}", f"-I{CSRC}", "-c", os.path.join(CSRC, src), "-o", obj]
+    if debug:
+        cmd.insert(1, "-DNRM_DEBUG_CHECKS")
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -61,25 +73,28 @@ def _compile(nvcc: str, src: str, obj: str, verbose: bool) -> None:
         sys.stderr.write(r.stderr)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Builds ``_build/libnrm.so`` if any input is newer; returns its path."""
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Builds ``_build/libnrm.so`` (or, with ``debug``, the checking variant
+    ``_build/libnrm_debug.so``) if any input is newer; returns its path."""
+    lib = DEBUG_LIB if debug else LIB
+    if not force and up_to_date(debug):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
-    objs = [os.path.join(BUILD, os.path.splitext(s)[0] + ".o") for s in SOURCES]
+    objdir = DEBUG_BUILD if debug else BUILD
+    os.makedirs(objdir, exist_ok=True)
+    objs = [os.path.join(objdir, os.path.splitext(s)[0] + ".o") for s in SOURCES]
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        futs = [ex.submit(_compile, nvcc, s, o, verbose) for s, o in zip(SOURCES, objs)]
+        futs = [ex.submit(_compile, nvcc, s, o, verbose, debug) for s, o in zip(SOURCES, objs)]
         for f in futs:
             f.result()
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread", "-ldl", "-lrt"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv, debug="--debug" in sys.argv))

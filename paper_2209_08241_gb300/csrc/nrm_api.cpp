@@ -640,6 +640,7 @@ const char* nrm_status_string(int status) {
     case NRM_ERR_OOM: return "NRM_ERR_OOM";
     case NRM_ERR_TIMEOUT: return "NRM_ERR_TIMEOUT";
     case NRM_ERR_NO_DEVICE: return "NRM_ERR_NO_DEVICE";
+    case NRM_ERR_BOUNDS: return "NRM_ERR_BOUNDS";
     default: return "NRM_ERR_UNKNOWN";
   }
 }
@@ -1573,6 +1574,27 @@ int nrm_selftest_wait_expiry(unsigned long long timeout_ns, float* elapsed_ms) {
   if (e1) cudaEventDestroy(e1);
   if (d) cudaFree(d);
   return rc;
+}
+
+int nrm_selftest_bounds(int* results) {
+  g_last_error.clear();
+  if (!results) return fail(NRM_ERR_INVALID_ARG, "results is NULL");
+  int* d = nullptr;
+  int host[9] = {0};
+  cudaError_t e = cudaMalloc(&d, 9 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(d, 0, 9 * sizeof(int));
+  if (e == cudaSuccess) e = nrm::launch_bounds_selftest(d, d + 8, 0);
+  if (e == cudaErrorNotSupported) {
+    cudaFree(d);
+    return fail(NRM_ERR_UNSUPPORTED, "not the checking build (build.py --debug)");
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(host, d, 9 * sizeof(int), cudaMemcpyDeviceToHost);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess) return fail(NRM_ERR_CUDA, "bounds self-test: %s", cudaGetErrorString(e));
+  for (int i = 0; i < 7; ++i) results[i] = host[i];
+  results[7] = host[8];  // the status word
+  return NRM_OK;
 }
 
 int nrm_sync_status(nrm_handle* h) {

@@ -92,9 +92,9 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d
   // in flight (the barrier that follows them publishes these too).
   for (int t = threadIdx.x; t < ex_w + ex_h; t += NT) {
     if (t < ex_w)
-      ucol[t] = ((float)(gx0 - alpha + t) - fd.cx) * fd.inv_fx;
+      NRM_STS(ucol + t, ((float)(gx0 - alpha + t) - fd.cx) * fd.inv_fx);
     else
-      vrow[t - ex_w] = ((float)(gy0 - alpha + t - ex_w) - fd.cy) * fd.inv_fy;
+      NRM_STS(vrow + t - ex_w, ((float)(gy0 - alpha + t - ex_w) - fd.cy) * fd.inv_fy);
   }
 
   if (fd.use_tma) {
@@ -127,8 +127,8 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d
         const int px = gx0 - alpha + ex;
         const bool in = px >= 0 && py >= 0 && px < W && py < H;
         const long long o = (long long)py * fd.out_pitch + px;
-        gw[ey * ex_w + ex] = in ? __ldg(gn + o) : make_float4(0.f, 0.f, 0.f, 0.f);
-        msk[ey * MW + ex + MP - alpha] = in ? __ldg(fd.valid + o) : (uint8_t)0;
+        NRM_STS(gw + ey * ex_w + ex, in ? __ldg(gn + o) : make_float4(0.f, 0.f, 0.f, 0.f));
+        NRM_STS(msk + ey * MW + ex + MP - alpha, in ? __ldg(fd.valid + o) : (uint8_t)0);
       }
     }
     __syncthreads();
@@ -153,11 +153,12 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d
   const uint8_t* msk_c = msk + MP - alpha;
   for (int i = threadIdx.x; i < n_ext; i += NT) {
     float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (msk_c[ey * MW + ex]) {
+    if (NRM_LDS(uint8_t, msk_c + ey * MW + ex)) {
       const float* pc = dep_c + ey * bw + ex;
-      const float d2 = pc[alpha], d4 = pc[-alpha], d3 = pc[alpha * bw], d5 = pc[-alpha * bw];
+      const float d2 = NRM_LDS(float, pc + alpha), d4 = NRM_LDS(float, pc - alpha);
+      const float d3 = NRM_LDS(float, pc + alpha * bw), d5 = NRM_LDS(float, pc - alpha * bw);
       const float S24 = d2 + d4, D24 = d2 - d4, S35 = d3 + d5, D35 = d3 - d5;
-      const float u1 = ucol[ex], v1 = vrow[ey];
+      const float u1 = NRM_LDS(float, ucol + ex), v1 = NRM_LDS(float, vrow + ey);
       const float A35 = ka * S35, B35 = kb * D35, C35 = kc * S35;
       const float A24 = ka * D24, B24 = kb * S24, C24 = kc * S24;
       const float nx = -A35 * D24, ny = -B24 * D35, P = C24 * S35;
@@ -165,7 +166,7 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d
       const float q = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
       const float inv = rsqrt_ftz(fmaxf(q, 1.17549435e-38f));
       const float hx0 = nx * inv, hy0 = ny * inv, hz0 = nz * inv;
-      float4 gv = gw[i];
+      float4 gv = NRM_LDS(float4, gw + i);
       if (scale) {
         gv.x *= sc;
         gv.y *= sc;
@@ -185,7 +186,7 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d
       w.z = fmaf(e_x, A35, c35);   // w4
       w.w = fmaf(e_y, B24, c24);   // w5
     }
-    gw[i] = w;
+    NRM_STS(gw + i, w);
     ey += step_rows;
     ex += step_cols;
     if (ex >= ex_w) {
@@ -203,8 +204,10 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d
       const int qx = gx0 + lx;
       if (qx >= W) break;
       const int c = (ly + alpha) * ex_w + (lx + alpha);
-      const float v = gw[c - alpha].x + gw[c + alpha].z + gw[c - alpha * ex_w].y + gw[c + alpha * ex_w].w;
-      grad[(long long)qy * fd.depth_pitch + qx] = v;
+      const float v = NRM_LDS(float4, gw + c - alpha).x + NRM_LDS(float4, gw + c + alpha).z +
+                      NRM_LDS(float4, gw + c - alpha * ex_w).y + NRM_LDS(float4, gw + c + alpha * ex_w).w;
+      float* q = grad + (long long)qy * fd.depth_pitch + qx;
+      if (NRM_GOK(q, grad, dbg_span(H, W, fd.depth_pitch, 4))) *q = v;
     }
   }
 }
@@ -214,6 +217,7 @@ __global__ void __launch_bounds__(NT)
     bwd_kernel(const __grid_constant__ FrameDesc fd, const __grid_constant__ BwdMaps maps, const Globals g,
                const float* scale) {
   extern __shared__ __align__(128) unsigned char smem[];
+  NRM_DEBUG_ENTRY(g.status);
   bwd_tile<ALPHA>(fd, &fd.tmap, &maps.grad, &maps.mask, blockIdx.x * TX, blockIdx.y * TY, g, smem, scale, 0);
 }
 
@@ -222,6 +226,7 @@ __global__ void __launch_bounds__(NT)
 template <int ALPHA>
 __global__ void __launch_bounds__(NT) bwd_batched_kernel(const BwdBatchArgs args, const Globals g, const float* scale) {
   extern __shared__ __align__(128) unsigned char smem[];
+  NRM_DEBUG_ENTRY(g.status);
   const int f = (int)blockIdx.y;
   const FrameDesc& fd = args.frames[f];
   const int tiles_x = fd.tiles_x;
@@ -251,6 +256,7 @@ template <int ALPHA>
 __global__ void __launch_bounds__(NT)
     bwd_batched_param_kernel(const __grid_constant__ BwdParamBatch pb, const Globals g, const float* scale) {
   extern __shared__ __align__(128) unsigned char smem[];
+  NRM_DEBUG_ENTRY(g.status);
   const int f = (int)blockIdx.y;
   const FrameDesc& fd = pb.frames[f];
   const int tiles_x = fd.tiles_x;

@@ -8,6 +8,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <cstdio>
+
 #include "nrm_internal.h"
 
 namespace nrm {
@@ -151,6 +153,84 @@ __device__ __forceinline__ void record_error(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
+// ------------------------------------------------------- checking build
+//
+// Built with NRM_DEBUG_CHECKS (build.py --debug), every shared-memory access of
+// the kernels and every global access that depends on frame geometry goes
+// through the macros below: an index outside its buffer skips the access,
+// prints the site and records NRM_ERR_BOUNDS in the launch's status word (its
+// address is kept per block by NRM_DEBUG_ENTRY). Nothing traps. In ordinary
+// builds the macros are the plain accesses.
+
+// Bytes spanned by an H x W buffer of esz-byte elements with row pitch `pitch`
+// (the extent the checks allow for an output or input buffer).
+__host__ __device__ __forceinline__ long long dbg_span(int H, int W, long long pitch, int esz) {
+  return H > 0 && W > 0 ? ((long long)(H - 1) * pitch + W) * esz : 0;
+}
+
+#ifdef NRM_DEBUG_CHECKS
+__device__ __forceinline__ int*& dbg_status_slot() {
+  __shared__ int* slot;
+  return slot;
+}
+static __device__ __noinline__ void dbg_fail(const char* what, int line, long long off, long long len) {
+  printf("NRM_BOUNDS %s (line %d): byte offset %lld outside [0, %lld), block %d, thread %d\n", what, line, off,
+         len, (int)blockIdx.x, (int)threadIdx.x);
+  record_error(dbg_status_slot(), NRM_ERR_BOUNDS);
+}
+// p lies, with `bytes` bytes, inside the block's dynamic shared memory.
+__device__ __forceinline__ bool dbg_smem_ok(const void* p, int bytes, const char* what, int line) {
+  extern __shared__ __align__(128) unsigned char dbg_dyn_smem[];  // the alignment of every kernel's own declaration, so both name the same address
+  uint32_t size;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(size));
+  const long long off = (long long)smem_u32(p) - (long long)smem_u32(dbg_dyn_smem);
+  if (off < 0 || off + bytes > (long long)size) {
+    dbg_fail(what, line, off, size);
+    return false;
+  }
+  return true;
+}
+// p lies, with `bytes` bytes, inside [lo, lo + len).
+__device__ __forceinline__ bool dbg_gmem_ok(const void* p, int bytes, const void* lo, long long len, const char* what,
+                                            int line) {
+  const long long off = (const char*)p - (const char*)lo;
+  if (off < 0 || off + bytes > len) {
+    dbg_fail(what, line, off, len);
+    return false;
+  }
+  return true;
+}
+// Index i of a fixed-size (static shared or local) array of n elements.
+__device__ __forceinline__ bool dbg_index_ok(long long i, long long n, const char* what, int line) {
+  if (i < 0 || i >= n) {
+    dbg_fail(what, line, i, n);
+    return false;
+  }
+  return true;
+}
+// At kernel entry: the status word the checks report to (all threads).
+#define NRM_DEBUG_ENTRY(status)                            \
+  do {                                                     \
+    if (threadIdx.x == 0) nrm::dev::dbg_status_slot() = (status); \
+    __syncthreads();                                       \
+  } while (0)
+#define NRM_LDS(T, p) (nrm::dev::dbg_smem_ok((p), (int)sizeof(T), "shared load", __LINE__) ? *(p) : T())
+#define NRM_STS(p, v)                                                              \
+  do {                                                                             \
+    if (nrm::dev::dbg_smem_ok((p), (int)sizeof(*(p)), "shared store", __LINE__)) *(p) = (v); \
+  } while (0)
+#define NRM_GOK(p, lo, len) nrm::dev::dbg_gmem_ok((p), (int)sizeof(*(p)), (lo), (len), "global access", __LINE__)
+#define NRM_IOK(i, n) nrm::dev::dbg_index_ok((i), (n), "array index", __LINE__)
+#else
+#define NRM_DEBUG_ENTRY(status) \
+  do {                          \
+  } while (0)
+#define NRM_LDS(T, p) (*(p))
+#define NRM_STS(p, v) (*(p) = (v))
+#define NRM_GOK(p, lo, len) true
+#define NRM_IOK(i, n) true
+#endif
+
 // -------------------------------------------------- per-pixel (adjoint path)
 
 // Stencil sums and differences of Eq. 4-6 (adjoint kernel).
@@ -184,7 +264,7 @@ __device__ __forceinline__ void load_tile_plain(InT* sm, int bw, int bh, const F
     const int x = x0 + lx, y = y0 + ly;
     InT v = InT(0);
     if (x >= 0 && y >= 0 && x < fd.W && y < fd.H) v = __ldg(src + (long long)y * fd.depth_pitch + x);
-    sm[i] = v;
+    NRM_STS(sm + i, v);
   }
 }
 
@@ -259,12 +339,12 @@ __device__ __forceinline__ void decode_tile(const float* __restrict__ src, float
                                             int rows, int /*src_pitch*/, int /*skip*/) {
   const int n = fw * rows;  // same geometry: a flat copy
   for (int i = threadIdx.x * 4; i < n; i += NT * 4) {
-    float4 v = *reinterpret_cast<const float4*>(src + i);
+    float4 v = NRM_LDS(float4, reinterpret_cast<const float4*>(src + i));
     v.x = decode_depth(v.x);
     v.y = decode_depth(v.y);
     v.z = decode_depth(v.z);
     v.w = decode_depth(v.w);
-    *reinterpret_cast<float4*>(dst + i) = v;
+    NRM_STS(reinterpret_cast<float4*>(dst + i), v);
   }
 }
 
@@ -276,13 +356,13 @@ __device__ __forceinline__ void decode_tile(const uint16_t* __restrict__ src, fl
   for (int gi = threadIdx.x; gi < n; gi += NT) {
     const int r = gi / gpr;
     const int c = (gi - r * gpr) << 2;
-    const uint2 raw = *reinterpret_cast<const uint2*>(src + r * src_pitch + skip + c);
+    const uint2 raw = NRM_LDS(uint2, reinterpret_cast<const uint2*>(src + r * src_pitch + skip + c));
     float4 v;
     v.x = decode_depth_u16(raw.x & 0xFFFFu);
     v.y = decode_depth_u16(raw.x >> 16);
     v.z = decode_depth_u16(raw.y & 0xFFFFu);
     v.w = decode_depth_u16(raw.y >> 16);
-    *reinterpret_cast<float4*>(dst + r * fw + c) = v;
+    NRM_STS(reinterpret_cast<float4*>(dst + r * fw + c), v);
   }
 }
 
@@ -305,7 +385,7 @@ __device__ __forceinline__ void load_tile_decoded(float* dst, int bw, int bh, co
       else
         v = decode_depth(raw);
     }
-    dst[i] = v;
+    NRM_STS(dst + i, v);
   }
 }
 
@@ -405,10 +485,10 @@ struct QuadStencil {
   __device__ __forceinline__ void operator()(const float* pa, const float* pb, float2 d1, float2& nx, float2& ny,
                                              float2& P) const {
     const float2 M1 = f2(-1.0f, -1.0f);
-    const float2 d2 = f2(pa[alpha], pb[alpha]);
-    const float2 d4 = f2(pa[-alpha], pb[-alpha]);
-    const float2 d3 = f2(pa[dv], pb[dv]);
-    const float2 d5 = f2(pa[-dv], pb[-dv]);
+    const float2 d2 = f2(NRM_LDS(float, pa + alpha), NRM_LDS(float, pb + alpha));
+    const float2 d4 = f2(NRM_LDS(float, pa - alpha), NRM_LDS(float, pb - alpha));
+    const float2 d3 = f2(NRM_LDS(float, pa + dv), NRM_LDS(float, pb + dv));
+    const float2 d5 = f2(NRM_LDS(float, pa - dv), NRM_LDS(float, pb - dv));
     (void)d1;
     // d2 - d4 as one fused (-1) d4 + d2: a single rounding, like a subtraction.
     const float2 S24 = __fadd2_rn(d2, d4), D24 = __ffma2_rn(M1, d4, d2);
@@ -454,8 +534,9 @@ __device__ __forceinline__ void emit_pair(const TileFrame& f, long long out_row,
     ca = ka ? ca : 0u;
     cb = kb ? cb : 0u;
     uint32_t* dst = reinterpret_cast<uint32_t*>(f.normals) + out_row + 64 * p;
-    if (FULL || cola) __stcs(dst, ca);
-    if (FULL || colb) __stcs(dst + 32, cb);
+    [[maybe_unused]] const long long nlen = dbg_span(f.H, f.W, f.out_pitch, 4);
+    if ((FULL || cola) && NRM_GOK(dst, f.normals, nlen)) __stcs(dst, ca);
+    if ((FULL || colb) && NRM_GOK(dst + 32, f.normals, nlen)) __stcs(dst + 32, cb);
     return;
   }
   const float2 inv = f2(rsqrt_ftz(q.x), rsqrt_ftz(q.y));
@@ -467,14 +548,16 @@ __device__ __forceinline__ void emit_pair(const TileFrame& f, long long out_row,
     const __half2 xya = __floats2half2_rn(va.x, va.y), zwa = __floats2half2_rn(va.z, 0.0f);
     const __half2 xyb = __floats2half2_rn(vb.x, vb.y), zwb = __floats2half2_rn(vb.z, 0.0f);
     uint2* dst = reinterpret_cast<uint2*>(f.normals) + out_row + 64 * p;
-    if (FULL || cola)
+    [[maybe_unused]] const long long nlen = dbg_span(f.H, f.W, f.out_pitch, 8);
+    if ((FULL || cola) && NRM_GOK(dst, f.normals, nlen))
       __stcs(dst, make_uint2(*reinterpret_cast<const uint32_t*>(&xya), *reinterpret_cast<const uint32_t*>(&zwa)));
-    if (FULL || colb)
+    if ((FULL || colb) && NRM_GOK(dst + 32, f.normals, nlen))
       __stcs(dst + 32, make_uint2(*reinterpret_cast<const uint32_t*>(&xyb), *reinterpret_cast<const uint32_t*>(&zwb)));
   } else {
     float4* dst = reinterpret_cast<float4*>(f.normals) + out_row + 64 * p;
-    if (FULL || cola) __stcs(dst, va);
-    if (FULL || colb) __stcs(dst + 32, vb);
+    [[maybe_unused]] const long long nlen = dbg_span(f.H, f.W, f.out_pitch, 16);
+    if ((FULL || cola) && NRM_GOK(dst, f.normals, nlen)) __stcs(dst, va);
+    if ((FULL || colb) && NRM_GOK(dst + 32, f.normals, nlen)) __stcs(dst + 32, vb);
   }
 }
 
@@ -492,15 +575,19 @@ __device__ __forceinline__ void emit_mask_row(const TileFrame& f, int gx0, int g
   const int gx = gx0 + first;
   uint8_t* mrow = f.valid + (long long)gy * f.out_pitch;
   if ((FULL || gx + CH <= f.W) && f.mask_align >= CH) {
+    [[maybe_unused]] const long long mlen = dbg_span(f.H, f.W, f.out_pitch, 1);
     if (CH == 2) {
-      __stcs(reinterpret_cast<unsigned short*>(mrow + gx), (unsigned short)bits_to_bytes4(bits));
+      unsigned short* mp = reinterpret_cast<unsigned short*>(mrow + gx);
+      if (NRM_GOK(mp, f.valid, mlen)) __stcs(mp, (unsigned short)bits_to_bytes4(bits));
     } else {
-      __stcs(reinterpret_cast<unsigned int*>(mrow + gx), bits_to_bytes4(bits));
+      unsigned int* mp = reinterpret_cast<unsigned int*>(mrow + gx);
+      if (NRM_GOK(mp, f.valid, mlen)) __stcs(mp, bits_to_bytes4(bits));
     }
   } else {
 #pragma unroll
     for (int j = 0; j < CH; ++j) {
-      if (gx + j < f.W) mrow[gx + j] = (uint8_t)((bits >> j) & 1u);
+      if (gx + j < f.W && NRM_GOK(mrow + gx + j, f.valid, dbg_span(f.H, f.W, f.out_pitch, 1)))
+        mrow[gx + j] = (uint8_t)((bits >> j) & 1u);
     }
   }
 }
@@ -555,7 +642,7 @@ __device__ __forceinline__ void compute_tile_with(const float* __restrict__ F, i
     for (int p = 0; p < NP; ++p) {
       const float* pa = row + 64 * p;
       const float* pb = pa + 32;
-      const float2 d1 = f2(pa[0], pb[0]);
+      const float2 d1 = f2(NRM_LDS(float, pa), NRM_LDS(float, pb));
       float2 nx, ny, P;
       st(pa, pb, d1, nx, ny, P);
       emit_pair<OUT, SECANT, FULL>(f, out_row, p, d1, nx, ny, P, nu1[p], ku[p], nv1, kv, T, tau2, colok[2 * p],
@@ -577,11 +664,12 @@ __device__ __forceinline__ void compute_tile_with(const float* __restrict__ F, i
       float4* prow = reinterpret_cast<float4*>(f.points) + (long long)gy * f.out_pitch + gx0 + lane;
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
-        const float d = row[32 * c];
+        const float d = NRM_LDS(float, row + 32 * c);
         const float z = d * f.point_scale;
         const float u1 = (c & 1) ? -nu1[c >> 1].y : -nu1[c >> 1].x;
         const float4 q = d == d ? make_float4(z * u1, z * v1, z, 0.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (FULL || colok[c]) __stcs(prow + 32 * c, q);
+        if ((FULL || colok[c]) && NRM_GOK(prow + 32 * c, f.points, dbg_span(f.H, f.W, f.out_pitch, 16)))
+          __stcs(prow + 32 * c, q);
       }
     }
   }

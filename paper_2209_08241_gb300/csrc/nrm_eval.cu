@@ -28,6 +28,7 @@ __device__ __forceinline__ void angles(float4 n, float& phi, float& theta) {
 __global__ void __launch_bounds__(kThreads)
     spherical_kernel(const float4* __restrict__ n, const uint8_t* __restrict__ valid, int H, int W,
                      long long pitch, float* __restrict__ phi, float* __restrict__ theta) {
+  NRM_DEBUG_ENTRY(nullptr);
   const int x = blockIdx.x * kThreads + threadIdx.x;
   if (x >= W) return;
   for (int y = blockIdx.y; y < H; y += gridDim.y) {
@@ -38,8 +39,8 @@ __global__ void __launch_bounds__(kThreads)
     const float4 nn = __ldg(n + o);
     float p = 0.0f, t = 0.0f;
     if (v) angles(nn, p, t);
-    __stcs(phi + o, p);
-    __stcs(theta + o, t);
+    if (NRM_GOK(phi + o, phi, dev::dbg_span(H, W, pitch, 4))) __stcs(phi + o, p);
+    if (NRM_GOK(theta + o, theta, dev::dbg_span(H, W, pitch, 4))) __stcs(theta + o, t);
   }
 }
 
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(kThreads)
   // Each thread sums its own pixels in FP32 (a few hundred terms at most for
   // frames up to 2^24 pixels: relative error ~1e-5), then the block and the
   // final pass add the per-thread sums in FP64.
+  NRM_DEBUG_ENTRY(nullptr);
   float st = 0.0f, sp = 0.0f;
   int cnt = 0;
   // All four loads of a pixel are independent of the masks, and the loop is
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(kThreads)
   }
   double dst = st, dsp = sp, dcnt = cnt;
   block_sum3(dst, dsp, dcnt);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && NRM_IOK(3 * (long long)blockIdx.x + 2, 3LL * kMseBlocks)) {
     partials[3 * blockIdx.x + 0] = dst;
     partials[3 * blockIdx.x + 1] = dsp;
     partials[3 * blockIdx.x + 2] = dcnt;
@@ -114,8 +116,9 @@ __global__ void __launch_bounds__(kThreads)
 
 __global__ void __launch_bounds__(kThreads) mse_final_kernel(const double* __restrict__ partials, int n,
                                                              double* __restrict__ out) {
+  NRM_DEBUG_ENTRY(nullptr);
   double st = 0.0, sp = 0.0, cnt = 0.0;
-  for (int i = threadIdx.x; i < n; i += kThreads) {
+  for (int i = threadIdx.x; i < n && NRM_IOK(3LL * i + 2, 3LL * kMseBlocks); i += kThreads) {
     st += partials[3 * i + 0];
     sp += partials[3 * i + 1];
     cnt += partials[3 * i + 2];

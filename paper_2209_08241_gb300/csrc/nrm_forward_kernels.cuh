@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(NT)
     fwd_plain_kernel(const __grid_constant__ FrameDesc fd, const Globals g) {
   static_assert(TX / 2 + TY <= NT, "one thread per table entry");
   extern __shared__ __align__(128) unsigned char smem[];
+  NRM_DEBUG_ENTRY(g.status);
   const int alpha = g.alpha;
   const bool u16 = fd.in_dtype == NRM_IN_U16_MM;
   const int eb = u16 ? 2 : 4;
@@ -99,6 +100,7 @@ __device__ __forceinline__ void persistent_pipeline(const BatchArgs& args, const
   const int my = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / G + 1 : 0;
   if (my == 0) return;
 
+  NRM_DEBUG_ENTRY(g.status);
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
@@ -131,6 +133,9 @@ __device__ __forceinline__ void persistent_pipeline(const BatchArgs& args, const
       const int ty = local / tiles_x;
       const int tx = local - ty * tiles_x;
       StageInfo& si = info[s];
+#ifdef NRM_DEBUG_CHECKS
+      if (!dbg_smem_ok(&si, (int)sizeof(StageInfo), "stage record", __LINE__)) return;
+#endif
       si.f = tile_frame(*fd, g.sign);
       si.tx = tx;
       si.ty = ty;
@@ -157,7 +162,7 @@ __device__ __forceinline__ void persistent_pipeline(const BatchArgs& args, const
   for (int i = 0; i < my; ++i) {
     const int s = i % S;
     const bool ok = mbar_wait_warp(smem_u32(&full[s]), (uint32_t)((i / S) & 1), g.timeout_ns);
-    const StageInfo si = info[s];
+    const StageInfo si = NRM_LDS(StageInfo, info + s);
     const bool u16 = si.f.in_dtype == NRM_IN_U16_MM;
     const int padx = pad_x(alpha, u16 ? 2 : 4);  // staging (TMA) box
     const int bw = TX + 2 * padx;

@@ -35,11 +35,11 @@ __device__ __forceinline__ void fill_tile_tables(float4* tab, const TileFrame& f
   if (t < TX / 2) {
     const float ua = ((float)(gx0 + 2 * t) - f.cx) * f.inv_fx;
     const float ub = ((float)(gx0 + 2 * t + 1) - f.cx) * f.inv_fx;
-    tab[t] = make_float4(-ua, -ub, fmaf(ua, ua, 1.0f), fmaf(ub, ub, 1.0f));
+    NRM_STS(tab + t, make_float4(-ua, -ub, fmaf(ua, ua, 1.0f), fmaf(ub, ub, 1.0f)));
   } else if (t < TX / 2 + TY) {
     const int r = t - TX / 2;
     const float v1 = ((float)(gy0 + r) - f.cy) * f.inv_fy;
-    tab[t] = make_float4(-v1, -v1, v1 * v1, v1 * v1);
+    NRM_STS(tab + t, make_float4(-v1, -v1, v1 * v1, v1 * v1));
   }
 }
 
@@ -69,14 +69,14 @@ __device__ __forceinline__ void decode_tile_u16_fixed(const uint16_t* __restrict
   const int g = lane % M;
   const float2 kb = f2(-8388607.0f, -8388607.0f);
   auto cvt4 = [&](const uint16_t* s, float* d) {
-    const uint2 raw = *reinterpret_cast<const uint2*>(s);
+    const uint2 raw = NRM_LDS(uint2, reinterpret_cast<const uint2*>(s));
     // (u - 1) | 0x4B000000 is the float 2^23 + u - 1 for u >= 1 and a NaN for
     // u = 0; subtracting 2^23 - 1 gives u exactly and keeps the NaN.
     const float2 lo = __fadd2_rn(f2(__uint_as_float(((raw.x & 0xFFFFu) - 1u) | 0x4B000000u),
                                     __uint_as_float(((raw.x >> 16) - 1u) | 0x4B000000u)), kb);
     const float2 hi = __fadd2_rn(f2(__uint_as_float(((raw.y & 0xFFFFu) - 1u) | 0x4B000000u),
                                     __uint_as_float(((raw.y >> 16) - 1u) | 0x4B000000u)), kb);
-    *reinterpret_cast<float4*>(d) = make_float4(lo.x, lo.y, hi.x, hi.y);
+    NRM_STS(reinterpret_cast<float4*>(d), make_float4(lo.x, lo.y, hi.x, hi.y));
   };
 #pragma unroll 1
   for (int r = warp * RP + lane / M; r < ROWS; r += NW * RP) cvt4(src + r * SP + 8 + 4 * g, dst + r * FW + 4 + 4 * g);
@@ -172,7 +172,7 @@ __device__ __forceinline__ void compute_tile_vec(const float* __restrict__ F, co
   float2 nu1[NP], ku[NP];
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
-    const float4 c = tab[xl / 2 + j];
+    const float4 c = NRM_LDS(float4, tab + xl / 2 + j);
     nu1[j] = f2(c.x, c.y);
     ku[j] = f2(c.z, c.w);
   }
@@ -196,30 +196,30 @@ __device__ __forceinline__ void compute_tile_vec(const float* __restrict__ F, co
     float rowv[V + 4];
     float up[V], dn[V];
     if (V == 4) {
-      const float4 c = *reinterpret_cast<const float4*>(p);
-      const float4 u = *reinterpret_cast<const float4*>(p - ALPHA * FW);
-      const float4 d = *reinterpret_cast<const float4*>(p + ALPHA * FW);
+      const float4 c = NRM_LDS(float4, reinterpret_cast<const float4*>(p));
+      const float4 u = NRM_LDS(float4, reinterpret_cast<const float4*>(p - ALPHA * FW));
+      const float4 d = NRM_LDS(float4, reinterpret_cast<const float4*>(p + ALPHA * FW));
       rowv[2] = c.x, rowv[3] = c.y, rowv[4] = c.z, rowv[5] = c.w;
       up[0] = u.x, up[1] = u.y, up[2] = u.z, up[3] = u.w;
       dn[0] = d.x, dn[1] = d.y, dn[2] = d.z, dn[3] = d.w;
     } else {
-      const float2 c = *reinterpret_cast<const float2*>(p);
-      const float2 u = *reinterpret_cast<const float2*>(p - ALPHA * FW);
-      const float2 d = *reinterpret_cast<const float2*>(p + ALPHA * FW);
+      const float2 c = NRM_LDS(float2, reinterpret_cast<const float2*>(p));
+      const float2 u = NRM_LDS(float2, reinterpret_cast<const float2*>(p - ALPHA * FW));
+      const float2 d = NRM_LDS(float2, reinterpret_cast<const float2*>(p + ALPHA * FW));
       rowv[2] = c.x, rowv[3] = c.y;
       up[0] = u.x, up[1] = u.y;
       dn[0] = d.x, dn[1] = d.y;
     }
     if (ALPHA == 2) {
-      const float2 l = *reinterpret_cast<const float2*>(p - 2);
-      const float2 r = *reinterpret_cast<const float2*>(p + V);
+      const float2 l = NRM_LDS(float2, reinterpret_cast<const float2*>(p - 2));
+      const float2 r = NRM_LDS(float2, reinterpret_cast<const float2*>(p + V));
       rowv[0] = l.x, rowv[1] = l.y;
       rowv[V + 2] = r.x, rowv[V + 3] = r.y;
     } else {
-      rowv[0] = 0.0f, rowv[1] = p[-1];
-      rowv[V + 2] = p[V], rowv[V + 3] = 0.0f;
+      rowv[0] = 0.0f, rowv[1] = NRM_LDS(float, p - 1);
+      rowv[V + 2] = NRM_LDS(float, p + V), rowv[V + 3] = 0.0f;
     }
-    const float4 rr = rtab[r0 + k * RSTEP];
+    const float4 rr = NRM_LDS(float4, rtab + r0 + k * RSTEP);
     const float2 nv1 = f2(rr.x, rr.y), kv = f2(rr.z, rr.w);
 
     uint32_t w[V * BPP / 4];
@@ -261,15 +261,22 @@ __device__ __forceinline__ void compute_tile_vec(const float* __restrict__ F, co
     }
     unsigned char* np_ = nptr + k * nstep;
     uint8_t* mp = mptr + k * mstep;
+    [[maybe_unused]] const long long nlen = dbg_span(f.H, f.W, f.out_pitch, BPP);
+    [[maybe_unused]] const long long mlen = dbg_span(f.H, f.W, f.out_pitch, 1);
     if (V * BPP == 16) {
-      __stcs(reinterpret_cast<uint4*>(np_), make_uint4(w[0], w[1], w[2], w[3]));
+      uint4* q = reinterpret_cast<uint4*>(np_);
+      if (NRM_GOK(q, f.normals, nlen)) __stcs(q, make_uint4(w[0], w[1], w[2], w[3]));
     } else {
-      __stcs(reinterpret_cast<uint2*>(np_), make_uint2(w[0], w[1]));
+      uint2* q = reinterpret_cast<uint2*>(np_);
+      if (NRM_GOK(q, f.normals, nlen)) __stcs(q, make_uint2(w[0], w[1]));
     }
-    if (V == 4)
-      __stcs(reinterpret_cast<unsigned int*>(mp), mbits);
-    else
-      __stcs(reinterpret_cast<unsigned short*>(mp), (unsigned short)mbits);
+    if (V == 4) {
+      unsigned int* q = reinterpret_cast<unsigned int*>(mp);
+      if (NRM_GOK(q, f.valid, mlen)) __stcs(q, mbits);
+    } else {
+      unsigned short* q = reinterpret_cast<unsigned short*>(mp);
+      if (NRM_GOK(q, f.valid, mlen)) __stcs(q, (unsigned short)mbits);
+    }
   }
 }
 

@@ -241,6 +241,9 @@ cudaError_t launch_multiscale_batched(const BatchArgs& args, const MsConsts& ms,
 // Bounded-wait self-test (nrm_selftest.cu): status2 = two device ints (zeroed
 // by the caller), one per wait flavour.
 cudaError_t launch_wait_expiry(unsigned long long timeout_ns, int* status2, cudaStream_t stream);
+// Range-check self-test (nrm_selftest.cu): cudaErrorNotSupported unless this is
+// the checking build (NRM_DEBUG_CHECKS).
+cudaError_t launch_bounds_selftest(int* results, int* status, cudaStream_t stream);
 
 // Plane-fitting ground truth (nrm_planefit.cu): FP32 normals (w = 0) and the
 // validity mask of the (2 radius + 1)^2 window fit; fd.depth, fd.normals,

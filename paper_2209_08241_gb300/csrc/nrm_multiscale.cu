@@ -78,7 +78,7 @@ __device__ __forceinline__ void ms_compute(const float* __restrict__ F, int fw, 
     float2 d1[NP], ax[NP], ay[NP], ap[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-      d1[p] = f2(row[64 * p], row[64 * p + 32]);
+      d1[p] = f2(NRM_LDS(float, row + 64 * p), NRM_LDS(float, row + 64 * p + 32));
       ax[p] = ay[p] = ap[p] = f2(-0.f, -0.f);
     }
 #pragma unroll 1
@@ -92,8 +92,8 @@ __device__ __forceinline__ void ms_compute(const float* __restrict__ F, int fw, 
       for (int p = 0; p < NP; ++p) {
         const float* pa = row + 64 * p;
         const float* pb = pa + 32;
-        const float2 d2 = f2(pa[al], pb[al]);
-        const float2 d3 = f2(pa[dv], pb[dv]);
+        const float2 d2 = f2(NRM_LDS(float, pa + al), NRM_LDS(float, pb + al));
+        const float2 d3 = f2(NRM_LDS(float, pa + dv), NRM_LDS(float, pb + dv));
         if (FORM == NRM_MS_PAIR) {
           // Eq. 1-3: A = -sign a/(K fy) s^2, B = -sign a/(K fx) s^2, C = sign a^2/(K fx fy) s^2.
           const float2 D21 = __ffma2_rn(M1, d1[p], d2), D31 = __ffma2_rn(M1, d1[p], d3);
@@ -102,8 +102,8 @@ __device__ __forceinline__ void ms_compute(const float* __restrict__ F, int fw, 
           ap[p] = __ffma2_rn(__fmul2_rn(C, d2), d3, ap[p]);
         } else {
           // Eq. 4-6: A = -sign a/(4 K fy) s^2, B = -sign a/(4 K fx) s^2, C = sign a^2/(4 K fx fy) s^2.
-          const float2 d4 = f2(pa[-al], pb[-al]);
-          const float2 d5 = f2(pa[-dv], pb[-dv]);
+          const float2 d4 = f2(NRM_LDS(float, pa - al), NRM_LDS(float, pb - al));
+          const float2 d5 = f2(NRM_LDS(float, pa - dv), NRM_LDS(float, pb - dv));
           const float2 S24 = __fadd2_rn(d2, d4), D24 = __ffma2_rn(M1, d4, d2);
           const float2 S35 = __fadd2_rn(d3, d5), D35 = __ffma2_rn(M1, d5, d3);
           ax[p] = __ffma2_rn(__fmul2_rn(A, S35), D24, ax[p]);
@@ -169,6 +169,7 @@ template <int OUT, int FORM>
 __global__ void __launch_bounds__(NT)
     fwd_ms_kernel(const __grid_constant__ FrameDesc fd, const __grid_constant__ MsConsts ms, const Globals g) {
   extern __shared__ __align__(128) unsigned char smem[];
+  NRM_DEBUG_ENTRY(g.status);
   const int alpha = ms.alpha_max;
   const int eb = fd.in_dtype == NRM_IN_U16_MM ? 2 : 4;
   const int padx = pad_x(alpha, eb);  // staging (TMA) box

@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(PT)
     plane_fit_kernel(const __grid_constant__ FrameDesc fd, float sign) {
   constexpr int tw = PX + 2 * R, th = PY + 2 * R;
   __shared__ __align__(16) float tile[tw * th];
+  NRM_DEBUG_ENTRY(nullptr);
   const int x0 = blockIdx.x * PX - R, y0 = blockIdx.y * PY - R;
   const bool u16 = fd.in_dtype == NRM_IN_U16_MM;
   for (int i = threadIdx.x; i < tw * th; i += PT) {
@@ -78,14 +79,15 @@ __global__ void __launch_bounds__(PT)
       z = u16 ? dev::decode_depth_u16(__ldg(reinterpret_cast<const uint16_t*>(fd.depth) + o))
               : dev::decode_depth(__ldg(reinterpret_cast<const float*>(fd.depth) + o));
     }
-    tile[i] = z;
+    if (NRM_IOK(i, tw * th)) tile[i] = z;
   }
   __syncthreads();
   const int lx = threadIdx.x & (PX - 1), ly = threadIdx.x / PX;
   const int px = blockIdx.x * PX + lx, py = blockIdx.y * PY + ly;
   if (px >= fd.W || py >= fd.H) return;
-  const float* c0 = tile + (ly + R) * tw + (lx + R);
-  const float z0 = c0[0];
+  const int ci = (ly + R) * tw + (lx + R);
+  const float* c0 = tile + ci;
+  const float z0 = NRM_IOK(ci, tw * th) ? c0[0] : 0.0f;
   const float u0 = ((float)px - fd.cx) * fd.inv_fx, v0 = ((float)py - fd.cy) * fd.inv_fy;
   float sx = 0.f, sy = 0.f, sz = 0.f;
   float a00 = 0.f, a01 = 0.f, a02 = 0.f, a11 = 0.f, a12 = 0.f, a22 = 0.f;
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(PT)
     const float ey = z0 * ((float)dy * fd.inv_fy);
 #pragma unroll
     for (int dx = -R; dx <= R; ++dx) {
-      const float dz = c0[dy * tw + dx] - z0;
+      const float dz = (NRM_IOK(ci + dy * tw + dx, tw * th) ? c0[dy * tw + dx] : 0.0f) - z0;
       const float qx = fmaf(dz, u0 + (float)dx * fd.inv_fx, z0 * ((float)dx * fd.inv_fx));
       const float qy = fmaf(dz, v, ey);
       sx += qx;
@@ -111,9 +113,11 @@ __global__ void __launch_bounds__(PT)
   }
   const long long oo = (long long)py * fd.out_pitch + px;
   float4* out = reinterpret_cast<float4*>(fd.normals) + oo;
+  [[maybe_unused]] const long long nlen = dev::dbg_span(fd.H, fd.W, fd.out_pitch, 16);
+  [[maybe_unused]] const long long mlen = dev::dbg_span(fd.H, fd.W, fd.out_pitch, 1);
   if (!(fabsf(sx) + fabsf(sy) + fabsf(sz) <= 3.402823466e38f)) {  // a NaN depth in the window
-    *out = make_float4(0.f, 0.f, 0.f, 0.f);
-    fd.valid[oo] = 0;
+    if (NRM_GOK(out, fd.normals, nlen)) *out = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (NRM_GOK(fd.valid + oo, fd.valid, mlen)) fd.valid[oo] = 0;
     return;
   }
   constexpr float inv_n = 1.0f / (float)((2 * R + 1) * (2 * R + 1));
@@ -151,8 +155,8 @@ __global__ void __launch_bounds__(PT)
   const float inv = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
   // Away from the camera (n . (u0, v0, 1) > 0), then the caller's orientation.
   const float o = (fmaf(nx, u0, fmaf(ny, v0, nz)) < 0.0f ? -inv : inv) * sign;
-  *out = make_float4(nx * o, ny * o, nz * o, 0.0f);
-  fd.valid[oo] = 1;
+  if (NRM_GOK(out, fd.normals, nlen)) *out = make_float4(nx * o, ny * o, nz * o, 0.0f);
+  if (NRM_GOK(fd.valid + oo, fd.valid, mlen)) fd.valid[oo] = 1;
 }
 
 }  // namespace

@@ -30,6 +30,42 @@ __global__ void __launch_bounds__(64) wait_expiry_kernel(unsigned long long time
 
 }  // namespace
 
+#ifdef NRM_DEBUG_CHECKS
+namespace {
+// The range checks of the checking build, evaluated on addresses inside and
+// just outside a block's dynamic shared memory (256 bytes at launch), an
+// 8-int global array and a 5-element index range. Only the addresses are
+// formed and compared; nothing outside a buffer is read or written.
+// results[0..6] = 1, 1, 0, 0, 1, 0, 0 when the checks are right; the failed
+// ones also record NRM_ERR_BOUNDS in *status.
+__global__ void __launch_bounds__(32) bounds_selftest_kernel(int* results, int* status) {
+  extern __shared__ __align__(128) unsigned char dyn[];
+  NRM_DEBUG_ENTRY(status);
+  if (threadIdx.x != 0) return;
+  results[0] = dbg_smem_ok(dyn, 4, "self-test", __LINE__);
+  results[1] = dbg_smem_ok(dyn + 252, 4, "self-test", __LINE__);
+  results[2] = dbg_smem_ok(dyn + 253, 4, "self-test (expected report)", __LINE__);
+  results[3] = dbg_smem_ok(dyn - 4, 4, "self-test (expected report)", __LINE__);
+  results[4] = dbg_gmem_ok(results + 7, 4, results, 32, "self-test", __LINE__);
+  results[5] = dbg_gmem_ok(results + 8, 4, results, 32, "self-test (expected report)", __LINE__);
+  results[6] = dbg_index_ok(5, 5, "self-test (expected report)", __LINE__);
+}
+}  // namespace
+#endif
+
+// results: 8 device ints (results[7] is left alone); status: one device int.
+cudaError_t launch_bounds_selftest(int* results, int* status, cudaStream_t stream) {
+#ifdef NRM_DEBUG_CHECKS
+  void* args[2] = {&results, &status};
+  return cudaLaunchKernel((const void*)bounds_selftest_kernel, dim3(1), dim3(32), args, 256, stream);
+#else
+  (void)results;
+  (void)status;
+  (void)stream;
+  return cudaErrorNotSupported;
+#endif
+}
+
 cudaError_t launch_wait_expiry(unsigned long long timeout_ns, int* status2, cudaStream_t stream) {
   void* args[2] = {&timeout_ns, &status2};
   return cudaLaunchKernel((const void*)wait_expiry_kernel, dim3(1), dim3(64), args, 0, stream);

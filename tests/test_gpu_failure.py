@@ -37,3 +37,21 @@ def test_selftest_rejects_out_of_range_limits():
     lib = nrm._lib.load()
     assert lib.nrm_selftest_wait_expiry(10, None) == nrm._lib.NRM_ERR_INVALID_ARG
     assert lib.nrm_selftest_wait_expiry(5_000_000_000, None) == nrm._lib.NRM_ERR_INVALID_ARG
+
+
+def test_bounds_selftest():
+    """In the checking build the range checks accept in-range and reject
+    out-of-range addresses (formed, never dereferenced) and record
+    NRM_ERR_BOUNDS; the ordinary build reports that it has no checks."""
+    import ctypes
+    import os
+    from paper_2209_08241_gb300 import _lib
+    lib = _lib.load()
+    res = (ctypes.c_int * 8)()
+    rc = lib.nrm_selftest_bounds(res)
+    if os.environ.get("NRM_LIB_VARIANT", "") == "debug":
+        assert rc == _lib.NRM_OK, lib.nrm_last_error()
+        assert list(res)[:7] == [1, 1, 0, 0, 1, 0, 0]
+        assert res[7] == _lib.NRM_ERR_BOUNDS
+    else:
+        assert rc == _lib.NRM_ERR_UNSUPPORTED
