@@ -1048,8 +1048,9 @@ def kernel_case(args):
     call and prints the mean time per call (CUDA events on the stream) and the
     algorithmic bandwidth; for timing and for ncu captures. Cases:
       forward           batched forward on --frames full-HD uint16 frames
-                        (default 8), normals as --out (f32, f16, oct16), launch
-                        geometry --config (default: the handle's)
+                        (default 8), normals as --out (f32, f16, oct16), with
+                        the point cloud if --points, launch geometry --config
+                        (default: the handle's)
       adjoint           single-frame adjoint, 4096 x 3072 float32
       adjoint_batch     batched adjoint, --frames 640 x 480 float32 (default 32)
       plane_fit         plane-fitting ground truth, --radius, 4096 x 3072
@@ -1084,6 +1085,8 @@ def kernel_case(args):
         b = nrm.BatchedEstimator(nrm.NormalParams(out_dtype=args.out if case == "forward" else "f32"))
         if case == "forward":
             outs = b(items)
+            if args.points:
+                outs = [(n, v, torch.empty_like(n)) for n, v in outs]
             if args.config:
                 b.set_config(*[int(v) for v in args.config.split(",")])
             arr, _ = b.make_frames(items, outs)
@@ -1095,7 +1098,7 @@ def kernel_case(args):
                 b.run(arr, frames)
             st = b.stats()
             ms = st["kernel_ms"] / max(1, st["launches"])
-            nbytes_px = 2 + OUT_BYTES[args.out] + 1
+            nbytes_px = 2 + OUT_BYTES[args.out] + 1 + (16 if args.points else 0)
         else:
             outs = b.multiscale(items, (1, 2, 3, 4), args.form)
             arr, _ = b.make_frames(items, outs)
@@ -1178,6 +1181,7 @@ def main(argv=None):
                     help="run one kernel for timing or profiling instead of the benchmark")
     ap.add_argument("--out", choices=sorted(OUT_BYTES), default="f32", help="normal output type (forward case)")
     ap.add_argument("--reps", type=int, default=20, help="timed calls (kernel cases)")
+    ap.add_argument("--points", action="store_true", help="also write the point cloud (forward case, f32 output)")
     ap.add_argument("--radius", type=int, default=2, help="window radius (plane_fit case)")
     ap.add_argument("--form", choices=["pair", "quad"], default="pair", help="stencil (multiscale cases)")
     args = ap.parse_args(argv)
