@@ -25,22 +25,40 @@ __device__ __forceinline__ void angles(float4 n, float& phi, float& theta) {
   theta = atan2f(sqrtf(fmaf(n.x, n.x, n.y * n.y)), n.z);
 }
 
+constexpr int kSphRows = 4;  // rows per thread of the angle-image kernel
+
 __global__ void __launch_bounds__(kThreads)
     spherical_kernel(const float4* __restrict__ n, const uint8_t* __restrict__ valid, int H, int W,
                      long long pitch, float* __restrict__ phi, float* __restrict__ theta) {
   NRM_DEBUG_ENTRY(nullptr);
   const int x = blockIdx.x * kThreads + threadIdx.x;
   if (x >= W) return;
-  for (int y = blockIdx.y; y < H; y += gridDim.y) {
-    const long long o = (long long)y * pitch + x;
-    // Both loads are issued before the mask is tested (one memory latency,
-    // not two in a row); a masked pixel's stored normal is (0, 0, 0, 0).
-    const uint8_t v = __ldg(valid + o);
-    const float4 nn = __ldg(n + o);
-    float p = 0.0f, t = 0.0f;
-    if (v) angles(nn, p, t);
-    if (NRM_GOK(phi + o, phi, dev::dbg_span(H, W, pitch, 4))) __stcs(phi + o, p);
-    if (NRM_GOK(theta + o, theta, dev::dbg_span(H, W, pitch, 4))) __stcs(theta + o, t);
+  // Each thread takes kSphRows rows of its column per step and issues all
+  // their loads (mask byte and normal, independent of the mask) before the
+  // first angle, so that several memory latencies overlap; a masked pixel's
+  // stored normal is (0, 0, 0, 0).
+  for (int y0 = blockIdx.y * kSphRows; y0 < H; y0 += gridDim.y * kSphRows) {
+    uint8_t v[kSphRows];
+    float4 nn[kSphRows];
+#pragma unroll
+    for (int r = 0; r < kSphRows; ++r) {
+      v[r] = 0;
+      nn[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (y0 + r < H) {
+        const long long o = (long long)(y0 + r) * pitch + x;
+        v[r] = __ldg(valid + o);
+        nn[r] = __ldg(n + o);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kSphRows; ++r) {
+      if (y0 + r >= H) break;
+      const long long o = (long long)(y0 + r) * pitch + x;
+      float p = 0.0f, t = 0.0f;
+      if (v[r]) angles(nn[r], p, t);
+      if (NRM_GOK(phi + o, phi, dev::dbg_span(H, W, pitch, 4))) __stcs(phi + o, p);
+      if (NRM_GOK(theta + o, theta, dev::dbg_span(H, W, pitch, 4))) __stcs(theta + o, t);
+    }
   }
 }
 
@@ -135,7 +153,8 @@ __global__ void __launch_bounds__(kThreads) mse_final_kernel(const double* __res
 
 cudaError_t launch_spherical(const float* normals, const uint8_t* valid, int H, int W, long long pitch, float* phi,
                              float* theta, cudaStream_t stream) {
-  dim3 grid((W + kThreads - 1) / kThreads, H < 65535 ? H : 65535);
+  const int row_steps = (H + kSphRows - 1) / kSphRows;
+  dim3 grid((W + kThreads - 1) / kThreads, row_steps < 65535 ? row_steps : 65535);
   const float4* n4 = reinterpret_cast<const float4*>(normals);
   void* args[7] = {&n4, &valid, &H, &W, &pitch, &phi, &theta};
   return cudaLaunchKernel((const void*)spherical_kernel, grid, dim3(kThreads), args, 0, stream);
