@@ -1,7 +1,8 @@
 """GPU evaluation kernels (Section 4: I_phi / I_theta images, MSE of Tables
 2-5) against the FP64 evaluation oracle on identical float32 normal maps.
 
-Tolerances: atan2f and sqrtf are within a few ulp, so angles agree to 4e-6 rad
+Tolerances: the kernels' arctangent (a polynomial fit after octant
+reduction, about 2e-7 rad) and sqrtf give angles within 4e-6 rad
 (absolute, phi compared modulo 2 pi). The MSE inputs keep every phi at least
 0.1 rad from the 0 / 2 pi cut, where a rounding difference could move a
 pixel's phi by 2 pi; there the MSE agrees to 1e-4 relative."""
@@ -56,6 +57,50 @@ def test_spherical_axis_directions():
     phi, theta = nrm.spherical_images(n, v)
     np.testing.assert_allclose(phi.cpu().numpy()[0], expect_phi, atol=4e-6)
     np.testing.assert_allclose(theta.cpu().numpy()[0], expect_th, atol=4e-6)
+
+
+def test_spherical_signed_zeros_and_octant_boundaries():
+    """atan2's conventions for signed zeros (-0 counts as negative x; the sign
+    of y is kept, so phi = -0 stays -0 and -pi wraps to pi), both zero, and
+    directions on the octant boundaries |x| = |y|, against the FP64 oracle on
+    the same float32 inputs, exactly where the result is 0 or pi."""
+    z, nz = 0.0, -0.0
+    r = math.sqrt(0.5)
+    dirs = [(z, z, 1), (nz, z, 1), (z, nz, 1), (nz, nz, 1), (-1, z, 0), (-1, nz, 0), (1, nz, 0), (1, z, 0),
+            (z, z, -1), (nz, z, -1), (r, r, 0), (-r, r, 0), (-r, -r, 0), (r, -r, 0), (r, r, -1e-30),
+            (1e-30, 1.0, 0), (-1e-30, 1.0, 0), (1.0, 1e-30, 0), (1.0, -1e-30, 0)]
+    n = torch.zeros((1, len(dirs), 4), dtype=torch.float32)
+    n[0, :, :3] = torch.tensor(dirs, dtype=torch.float32)
+    v = torch.ones((1, len(dirs)), dtype=torch.uint8)
+    phi, theta = nrm.spherical_images(n.to(DEV), v.to(DEV))
+    rp, rt = evaluation.spherical(n.double().numpy(), v.numpy())
+    gp, gt = phi.double().cpu().numpy(), theta.double().cpu().numpy()
+    np.testing.assert_allclose(gp, rp, atol=4e-6, rtol=0)
+    np.testing.assert_allclose(gt, rt, atol=4e-6, rtol=0)
+    exact = (rp == 0) | (np.abs(rp - math.pi) < 1e-12)
+    assert (np.abs(gp[exact] - rp[exact]) <= 2.5e-7).all()
+    # phi = -1e-30 + 2 pi rounds to 2 pi itself (float32 here, float64 in the
+    # oracle): the top of the range is reached only by such rounding.
+    assert float(phi.max()) <= float(np.float32(2 * math.pi)) and float(phi.min()) >= -0.0
+
+
+def test_spherical_dense_direction_sweep():
+    """Unit normals on a dense grid of directions (every octant, both poles):
+    both angle images within 4e-6 rad of the FP64 oracle (phi modulo 2 pi)."""
+    ph = np.linspace(0.0, 2 * math.pi, 1441)
+    th = np.linspace(0.0, math.pi, 721)
+    P, T = np.meshgrid(ph, th)
+    n = np.zeros(P.shape + (4,), np.float32)
+    n[..., 0] = np.sin(T) * np.cos(P)
+    n[..., 1] = np.sin(T) * np.sin(P)
+    n[..., 2] = np.cos(T)
+    v = np.ones(P.shape, np.uint8)
+    phi, theta = nrm.spherical_images(torch.from_numpy(n).to(DEV), torch.from_numpy(v).to(DEV))
+    rp, rt = evaluation.spherical(n.astype(np.float64), v)
+    dp = np.abs(phi.double().cpu().numpy() - rp)
+    dp = np.minimum(dp, 2 * math.pi - dp)
+    assert dp.max() <= 4e-6
+    assert np.abs(theta.double().cpu().numpy() - rt).max() <= 4e-6
 
 
 @pytest.mark.parametrize("shape", [(1, 1), (7, 300), (480, 640), (1080, 1920)])
