@@ -8,6 +8,7 @@
 // status word and the autotuner with its JSON cache.
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <cmath>
@@ -530,7 +531,10 @@ std::map<std::string, std::string> read_cache(const char* path) {
 }
 
 bool write_cache(const char* path, const std::map<std::string, std::string>& m) {
-  std::string tmp = std::string(path) + ".tmp";
+  // A temporary name of this process's own, then an atomic rename: processes
+  // that tune at the same time (one per GPU) never mix their writes; the
+  // last rename wins.
+  std::string tmp = std::string(path) + ".tmp." + std::to_string((long long)getpid());
   std::ofstream out(tmp);
   if (!out) return false;
   out << "{\n";
