@@ -53,6 +53,7 @@ __device__ __forceinline__ void angles(float4 n, float& phi, float& theta) {
 }
 
 constexpr int kSphRows = 4;  // rows per thread of the angle-image kernel
+constexpr int kMsePx = 4;    // pixels per thread and step of the MSE kernel
 
 __global__ void __launch_bounds__(kThreads)
     spherical_kernel(const float4* __restrict__ n, const uint8_t* __restrict__ valid, int H, int W,
@@ -129,24 +130,39 @@ __global__ void __launch_bounds__(kThreads)
   NRM_DEBUG_ENTRY(nullptr);
   float st = 0.0f, sp = 0.0f;
   int cnt = 0;
-  // All four loads of a pixel are independent of the masks, and the loop is
-  // unrolled, so several pixels' loads are in flight before the first mask
-  // test; the sums still run over the pixels in the same order.
+  // A thread takes kMsePx pixels of a row (kThreads apart) per step and issues
+  // all their loads (masks and normals, independent of the masks) before the
+  // first angle, so that the memory latencies overlap; the sums still run
+  // over the thread's pixels in increasing column order.
   for (int y = blockIdx.x; y < H; y += gridDim.x) {
     const long long row = (long long)y * pitch;
-#pragma unroll 4
-    for (int x = threadIdx.x; x < W; x += kThreads) {
-      const long long o = row + x;
-      const uint8_t a = __ldg(va + o), b = __ldg(vb + o);
-      const float4 ma = __ldg(na + o), mb = __ldg(nb + o);
-      if (a && b) {
-        float pa, ta, pb, tb;
-        angles(ma, pa, ta);
-        angles(mb, pb, tb);
-        const float dt = ta - tb, dp = pa - pb;
-        st = fmaf(dt, dt, st);
-        sp = fmaf(dp, dp, sp);
-        ++cnt;
+    for (int x0 = threadIdx.x; x0 < W; x0 += kMsePx * kThreads) {
+      uint8_t a[kMsePx], b[kMsePx];
+      float4 ma[kMsePx], mb[kMsePx];
+#pragma unroll
+      for (int k = 0; k < kMsePx; ++k) {
+        const int x = x0 + k * kThreads;
+        a[k] = b[k] = 0;
+        ma[k] = mb[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (x < W) {
+          const long long o = row + x;
+          a[k] = __ldg(va + o);
+          b[k] = __ldg(vb + o);
+          ma[k] = __ldg(na + o);
+          mb[k] = __ldg(nb + o);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kMsePx; ++k) {
+        if (a[k] && b[k]) {
+          float pa, ta, pb, tb;
+          angles(ma[k], pa, ta);
+          angles(mb[k], pb, tb);
+          const float dt = ta - tb, dp = pa - pb;
+          st = fmaf(dt, dt, st);
+          sp = fmaf(dp, dp, sp);
+          ++cnt;
+        }
       }
     }
   }
