@@ -213,6 +213,12 @@ class NormalEstimator(_Handle):
         params = params or NormalParams(**kw)
         super().__init__(K, H, W, params, {"f32": NRM_IN_F32_M, "u16": NRM_IN_U16_MM}[in_dtype], device)
         self.K = tuple(float(v) for v in K)
+        # What every call checks, formed once (the per-frame call is host-bound).
+        self._dev_index = self.device.index
+        self._depth_dtype = torch.float32 if self.in_dtype == NRM_IN_F32_M else torch.uint16
+        self._hw = (self.H, self.W)
+        self._nshape = (self.H, self.W, self.params.out_channels)
+        self._ndtype = self.params.torch_out_dtype
 
     def new_outputs(self):
         """A new (normals, valid) pair of this estimator's size and output dtype."""
@@ -222,19 +228,25 @@ class NormalEstimator(_Handle):
         return n, m
 
     def _check_depth(self, depth: torch.Tensor):
-        _check_cuda(depth, "depth", self.device)
-        if tuple(depth.shape) != (self.H, self.W) or not depth.is_contiguous():
+        if depth.get_device() != self._dev_index:  # -1 for host tensors
+            _check_cuda(depth, "depth", self.device)
+        if depth.shape != self._hw or not depth.is_contiguous():
             raise ValueError(f"depth must be a contiguous ({self.H}, {self.W}) tensor")
-        if _in_dtype(depth) != self.in_dtype:
+        if depth.dtype != self._depth_dtype:
+            _in_dtype(depth)  # raises for a dtype the library does not take
             raise TypeError("depth dtype does not match the estimator's in_dtype")
 
     def _outputs(self, normals: torch.Tensor | None, valid: torch.Tensor | None):
         """The caller's (normals, valid), checked, or new ones."""
         if normals is None or valid is None:
             return self.new_outputs()
-        _check_dense(normals, (self.H, self.W, self.params.out_channels), self.params.torch_out_dtype, self.device,
-                     "normals")
-        _check_dense(valid, (self.H, self.W), torch.uint8, self.device, "valid")
+        # The common case in a few attribute reads; anything off goes through
+        # the full check, which raises with the details.
+        if not (normals.get_device() == self._dev_index and valid.get_device() == self._dev_index
+                and normals.shape == self._nshape and valid.shape == self._hw and normals.dtype == self._ndtype
+                and valid.dtype == torch.uint8 and normals.is_contiguous() and valid.is_contiguous()):
+            _check_dense(normals, self._nshape, self._ndtype, self.device, "normals")
+            _check_dense(valid, self._hw, torch.uint8, self.device, "valid")
         return normals, valid
 
     def estimate(self, depth: torch.Tensor, normals: torch.Tensor | None = None,
