@@ -230,7 +230,7 @@ NRM_API int nrm_backward_batched_scaled(nrm_handle* h, const nrm_grad_frame* fra
 /* Spherical angle images of a normal map (Section 4, the I_phi and I_theta
  * images, normalised to [0, 2 pi]): for each valid pixel
  *   phi = atan2(n_y, n_x) in [0, 2 pi),  theta = atan2(sqrt(n_x^2 + n_y^2), n_z) in [0, pi];
- * masked pixels get 0. Each angle is within about 2e-7 rad of the exact
+ * masked pixels get 0. Each angle is within about 3e-7 rad of the exact
  * value of its float32 inputs (atan2's signed-zero conventions included;
  * phi may round up to 2 pi itself just below the cut). normals: H x W x 4
  * float32; valid: H x W bytes; phi and theta: H x W float32; one pitch

@@ -2,7 +2,7 @@
 2-5) against the FP64 evaluation oracle on identical float32 normal maps.
 
 Tolerances: the kernels' arctangent (a polynomial fit after octant
-reduction, about 2e-7 rad) and sqrtf give angles within 4e-6 rad
+reduction, about 3e-7 rad) and sqrtf give angles within 4e-6 rad
 (absolute, phi compared modulo 2 pi). The MSE inputs keep every phi at least
 0.1 rad from the 0 / 2 pi cut, where a rounding difference could move a
 pixel's phi by 2 pi; there the MSE agrees to 1e-4 relative."""
