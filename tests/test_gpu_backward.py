@@ -30,7 +30,7 @@ def loss_grad(n, m, t):
     return g
 
 
-@pytest.mark.parametrize("alpha", [1, 2, 3])
+@pytest.mark.parametrize("alpha", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("orient", [False, True])
 def test_adjoint_matches_complex_step_oracle(alpha, orient):
     d, K = frame(alpha)
