@@ -109,15 +109,17 @@ bool encode_depth_map(CUtensorMap* m, const void* base, int in_dtype, int W, int
                       2, base, dims, strides, box);
 }
 
-// Upstream gradient of the adjoint (float4 per pixel) as a 3-D float32 tensor
-// (4, W, H); box (4, box_w, box_h) lands in shared memory as float4 per pixel.
+// Upstream gradient of the adjoint (float4 per pixel) as a 2-D tensor of
+// 8-byte elements (two per pixel): box (2 box_w, box_h) lands in shared memory
+// as float4 per pixel, each box row one contiguous run of 16 box_w bytes (a
+// 3-D float32 view with the 4 components innermost would move 16-byte rows).
 bool encode_grad_map(CUtensorMap* m, const void* base, int W, int H, long long out_pitch, int box_w,
                      int box_h) {
   if ((uintptr_t)base % 16) return false;
-  const cuuint64_t dims[3] = {4, (cuuint64_t)W, (cuuint64_t)H};
-  const cuuint64_t strides[2] = {16, (cuuint64_t)out_pitch * 16};
-  const cuuint32_t box[3] = {4, (cuuint32_t)box_w, (cuuint32_t)box_h};
-  return encode_tiled(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box);
+  const cuuint64_t dims[2] = {2 * (cuuint64_t)W, (cuuint64_t)H};
+  const cuuint64_t strides[1] = {(cuuint64_t)out_pitch * 16};
+  const cuuint32_t box[2] = {2 * (cuuint32_t)box_w, (cuuint32_t)box_h};
+  return encode_tiled(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, base, dims, strides, box);
 }
 
 // The mask (one byte per pixel, pitch out_pitch) as a 2-D uint8 tensor.

@@ -16,8 +16,8 @@
 //
 // One CTA per 64 x 32 output tile. Three TMA loads on one mbarrier stage the
 // tile's inputs in shared memory: the depth halo of radius 2 alpha, the upstream
-// gradient of the tile extended by alpha (a 3-D float32 box: 4 components x
-// columns x rows, i.e. float4 per pixel) and the mask of the same region (a
+// gradient of the tile extended by alpha (a 2-D box of 8-byte elements, two per
+// pixel, i.e. float4 per pixel) and the mask of the same region (a
 // uint8 box starting 16 columns left of the tile, the alignment TMA needs).
 // Phase 1 turns each staged gradient into the four weights in place; phase 2
 // gathers. Frames whose buffers cannot be TMA-mapped use plain loads into the
@@ -107,7 +107,7 @@ __device__ __forceinline__ void bwd_tile(const FrameDesc& fd, const void* tmap_d
     if (threadIdx.x == 0) {
       mbar_arrive_expect_tx(b, (uint32_t)(bw * bh * 4 + ex_w * ex_h * 16 + MW * ex_h));
       tma_load_2d(smem_u32(dep), tmap_d, gx0 - p2, gy0 - 2 * alpha, b);
-      tma_load_3d(smem_u32(gw), tmap_g, 0, gx0 - alpha, gy0 - alpha, b);
+      tma_load_2d(smem_u32(gw), tmap_g, 2 * (gx0 - alpha), gy0 - alpha, b);  // x in 8-byte units: even
       tma_load_2d(smem_u32(msk), tmap_m, gx0 - MP, gy0 - alpha, b);
     }
     const bool ok = mbar_wait_warp(b, 0, g.timeout_ns);

@@ -117,16 +117,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int 
       : "memory");
 }
 
-// 3-D tiled TMA load of box (x, y, z); x * element size must be a multiple of 16.
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, int x, int y, int z,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(bar)
-      : "memory");
-}
-
 // Named barrier over `count` threads (a multiple of 32) that also ORs a
 // predicate across them.
 __device__ __forceinline__ bool bar_red_or(uint32_t id, uint32_t count, bool pred) {

@@ -163,8 +163,8 @@ constexpr int kBwdMaskPad = 16;
 constexpr int kBwdMaskBoxW = kBwdTileX + 2 * kBwdMaskPad;
 
 // The adjoint's two further tensor maps per frame: the upstream gradient as a
-// 3-D float32 tensor (4, W, H), box (4, TX + 2 alpha, TY + 2 alpha), and the
-// mask as a 2-D uint8 tensor, box (kBwdMaskBoxW, TY + 2 alpha).
+// 2-D tensor of 8-byte elements (2 W, H), box (2 (TX + 2 alpha), TY + 2 alpha),
+// and the mask as a 2-D uint8 tensor, box (kBwdMaskBoxW, TY + 2 alpha).
 struct alignas(128) BwdMaps {
   CUtensorMap grad;
   CUtensorMap mask;
