@@ -193,6 +193,35 @@ def test_unaligned_pitches_use_plain_loads_and_byte_stores():
     assert torch.equal(n_wide[:, :W], n) and torch.equal(m_wide[:, :W], m)
 
 
+@pytest.mark.parametrize("out", ["f16", "oct16"])
+@pytest.mark.parametrize("alpha", [1, 2, 3])
+def test_vector_and_scalar_tile_loops_give_the_same_bits(out, alpha):
+    """half4 and octahedral outputs of full tiles take the vector tile loop
+    (alpha 1 or 2, aligned outputs); an odd row pitch (mask stores not
+    aligned) sends the same frames through the scalar loop, and alpha 3 takes
+    it everywhere. Every compiled tile shape, uint16 and float32 input: both
+    loops give the same bits."""
+    items = [scenes.random_frame(930 + i, W, H, DEV, kind=kind)
+             for i, (W, H, kind) in enumerate([(640, 480, "u16"), (517, 300, "f32"), (1920, 1080, "u16")])]
+    C = 2 if out == "oct16" else 4
+    dt = torch.int16 if out == "oct16" else torch.float16
+    b = nrm.BatchedEstimator(nrm.NormalParams(alpha=alpha, out_dtype=out))
+    for cfg in [(128, 16, 256), (64, 64, 256), (128, 64, 512), (64, 16, 128)]:
+        b.set_config(*cfg, stages=3)
+        vec = b(items)
+        outs = []
+        for d, _ in items:
+            H, W = d.shape
+            nb = torch.zeros((H, W + 1, C), dtype=dt, device=DEV)
+            vb = torch.zeros((H, W + 1), dtype=torch.uint8, device=DEV)
+            outs.append((nb[:, :W], vb[:, :W]))
+        sca = b(items, outputs=outs)
+        b.sync_status()
+        for (n1, m1), (n2, m2) in zip(vec, sca):
+            assert torch.equal(m1, m2), (out, alpha, cfg)
+            assert torch.equal(n1, n2), (out, alpha, cfg)
+
+
 @pytest.mark.parametrize("out", ["f32", "f16"])
 def test_mixed_size_batch_parity(out):
     """A batch drawn from the uneven size mix (with a 4096 x 3072 frame), float32
