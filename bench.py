@@ -738,8 +738,8 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
 
     gfr, _ = db.make_grad_frames(items, glist, vlist, dlist)
     # dL/dn_hat = -t / N_valid on valid pixels. The fused entry reads the
-    # targets t (float4) and the per-frame scale -1 / N_valid, so the step is:
-    # forward, the valid-pixel count of each frame, adjoint.
+    # targets t (float4) and the per-frame scale -1 / N_valid, so the step is
+    # three launches: forward, the per-frame scale from the masks, adjoint.
     tg4 = torch.zeros((Nd, Hd, Wd, 4), device=dev)
     tg4[..., :3] = tg
     tfr, _ = db.make_grad_frames(items, [tg4[i] for i in range(Nd)], vlist, dlist)
@@ -747,7 +747,7 @@ def bench_extras(args, dist, est, nrm, scenes, depth, Ks, normals, valid, frames
 
     def fwd_bwd():
         db.run(dfr, Nd, stream)
-        torch.reciprocal(vbuf.sum(dim=(1, 2), dtype=torch.float32).clamp_(min=1.0), out=scl).neg_()
+        db.cosine_loss_scale(tfr, Nd, scl, stream)
         db.run_backward_scaled(tfr, Nd, scl, stream)
 
     for _ in range(3):

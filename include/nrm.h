@@ -227,6 +227,18 @@ NRM_API int nrm_backward_batched(nrm_handle* h, const nrm_grad_frame* frames, in
 NRM_API int nrm_backward_batched_scaled(nrm_handle* h, const nrm_grad_frame* frames, int n, const float* scale,
                                         void* cuda_stream);
 
+/* The per-frame factor of that cosine loss: scale[i] = -1 / max(N_valid(i), 1),
+ * N_valid(i) the number of nonzero bytes of frames[i].valid (H x W, pitch
+ * out_pitch pixels; the other fields are not read). One launch per 128
+ * frames; the count is exact (integer sums) and the division is IEEE float32,
+ * so the result equals -1 / max(N, 1) formed in float32. scale: n floats of
+ * device memory (4-byte aligned), written asynchronously on the stream, where
+ * nrm_backward_batched_scaled on the same stream then reads it. Uses counters
+ * owned by the handle (allocated on first use and when n grows): calls on one
+ * handle must not overlap on the GPU. n = 0 is a no-op. */
+NRM_API int nrm_cosine_loss_scale(nrm_handle* h, const nrm_grad_frame* frames, int n, float* scale,
+                                  void* cuda_stream);
+
 /* Spherical angle images of a normal map (Section 4, the I_phi and I_theta
  * images, normalised to [0, 2 pi]): for each valid pixel
  *   phi = atan2(n_y, n_x) in [0, 2 pi),  theta = atan2(sqrt(n_x^2 + n_y^2), n_z) in [0, pi];

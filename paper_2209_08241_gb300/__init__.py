@@ -521,16 +521,27 @@ class BatchedEstimator(_Handle):
         _lib.check(self.lib.nrm_backward_batched_scaled(self.h, grad_frames_array, int(n), scale.data_ptr(),
                                                         _stream_ptr(stream)), "nrm_backward_batched_scaled")
 
+    def cosine_loss_scale(self, grad_frames_array, n: int, scale: torch.Tensor | None = None, stream=None):
+        """``nrm_cosine_loss_scale``: the (n,) float32 device tensor of
+        -1 / max(N_valid, 1) per frame of a grad-frame array (its masks), for
+        ``run_backward_scaled``; written asynchronously on the stream."""
+        if scale is None:
+            scale = torch.empty(int(n), dtype=torch.float32, device=self.device)
+        _check_dense(scale, (int(n),), torch.float32, self.device, "scale")
+        _lib.check(self.lib.nrm_cosine_loss_scale(self.h, grad_frames_array, int(n), scale.data_ptr(),
+                                                  _stream_ptr(stream)), "nrm_cosine_loss_scale")
+        return scale
+
     def cosine_loss_backward(self, items: Sequence, targets: Sequence, valids: Sequence,
                              grad_depths: Sequence | None = None, stream=None):
         """Depth gradients of L_i = mean over the valid pixels of frame i of
-        (1 - n_hat . t) for each frame i of a batch, in one adjoint launch with
-        no dL/dn_hat buffer: targets [(H, W, 4) float32 unit normals, 4th
-        component ignored], valids the forward's masks. Returns the gradients
-        and the per-frame scale -1 / max(N_valid, 1) it used."""
+        (1 - n_hat . t) for each frame i of a batch: the per-frame factor
+        -1 / max(N_valid, 1) (``nrm_cosine_loss_scale``), then one adjoint
+        launch with no dL/dn_hat buffer: targets [(H, W, 4) float32 unit
+        normals, 4th component ignored], valids the forward's masks. Returns
+        the gradients and the per-frame scale it used."""
         arr, outs = self.make_grad_frames(items, targets, valids, grad_depths)
-        counts = torch.stack([v.sum(dtype=torch.float32) for v in valids]) if valids else torch.empty(0)
-        scale = (-1.0 / counts.clamp(min=1.0)).to(torch.float32).contiguous()
+        scale = self.cosine_loss_scale(arr, len(items), stream=stream)
         self.run_backward_scaled(arr, len(items), scale, stream)
         return outs, scale
 

@@ -90,6 +90,7 @@ SIGNATURES = [
     ("nrm_backward_batched", ctypes.c_int, [_H, ctypes.POINTER(GradFrame), ctypes.c_int, _S]),
     ("nrm_backward_batched_scaled", ctypes.c_int, [_H, ctypes.POINTER(GradFrame), ctypes.c_int, ctypes.c_void_p,
                                                    _S]),
+    ("nrm_cosine_loss_scale", ctypes.c_int, [_H, ctypes.POINTER(GradFrame), ctypes.c_int, ctypes.c_void_p, _S]),
     ("nrm_spherical", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, _S]),
     ("nrm_angle_mse", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

@@ -283,6 +283,9 @@ struct nrm_handle {
   nrm_stats stats = {0, 0.0, 0};
   cudaEvent_t last_single = nullptr;  // after the latest plain / backward launch
   double* d_mse_partials = nullptr;   // nrm_angle_mse scratch (3 kMseBlocks doubles)
+  unsigned* d_loss_counters = nullptr; // nrm_cosine_loss_scale: 2 x loss_cap zeroed words
+  int loss_cap = 0;
+  std::vector<nrm::LossCountFrame> scratch_loss;
   HostLane lanes[kLanes];             // nrm_estimate_batched_host pipeline
   cudaEvent_t host_start = nullptr;
   std::vector<FrameDesc> scratch_desc;
@@ -815,6 +818,7 @@ void nrm_destroy(nrm_handle* h) {
   if (h->host_start) cudaEventDestroy(h->host_start);
   if (h->d_status) cudaFree(h->d_status);
   if (h->d_mse_partials) cudaFree(h->d_mse_partials);
+  if (h->d_loss_counters) cudaFree(h->d_loss_counters);
   delete h;
 }
 
@@ -1193,6 +1197,42 @@ int nrm_backward_batched_scaled(nrm_handle* h, const nrm_grad_frame* frames, int
   if (n > 0 && !scale) return fail(NRM_ERR_INVALID_ARG, "scale is NULL");
   if ((uintptr_t)scale % 4) return fail(NRM_ERR_INVALID_ARG, "scale not 4-byte aligned");
   return backward_batched(h, frames, n, scale, cuda_stream);
+}
+
+int nrm_cosine_loss_scale(nrm_handle* h, const nrm_grad_frame* frames, int n, float* scale, void* cuda_stream) {
+  g_last_error.clear();
+  if (!h) return fail(NRM_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 0) return fail(NRM_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return NRM_OK;
+  if (!frames || !scale) return fail(NRM_ERR_INVALID_ARG, "frames or scale is NULL");
+  if ((uintptr_t)scale % 4) return fail(NRM_ERR_INVALID_ARG, "scale not 4-byte aligned");
+  std::vector<nrm::LossCountFrame>& cf = h->scratch_loss;
+  cf.resize((size_t)n);
+  for (int i = 0; i < n; ++i) {
+    const nrm_grad_frame& f = frames[i];
+    if (f.H < 0 || f.W < 0) return fail(NRM_ERR_INVALID_ARG, "frame %d: negative size", i);
+    const bool empty = (long long)f.H * f.W == 0;
+    if (!empty && !f.valid) return fail(NRM_ERR_INVALID_ARG, "frame %d: valid is NULL", i);
+    if (!empty && f.out_pitch < f.W) return fail(NRM_ERR_INVALID_ARG, "frame %d: pitch < W", i);
+    cf[i] = {f.valid, empty ? 0 : f.H, empty ? 0 : f.W, f.out_pitch};
+  }
+  DeviceGuard guard(h->device);
+  if (n > h->loss_cap) {
+    if (h->d_loss_counters) {
+      NRM_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");  // earlier calls may still use the counters
+      cudaFree(h->d_loss_counters);
+      h->d_loss_counters = nullptr;
+      h->loss_cap = 0;
+    }
+    const int cap = std::max(n, 64);
+    NRM_CUDA(cudaMalloc(&h->d_loss_counters, sizeof(unsigned) * 2 * (size_t)cap), "cudaMalloc");
+    NRM_CUDA(cudaMemset(h->d_loss_counters, 0, sizeof(unsigned) * 2 * (size_t)cap), "cudaMemset");
+    h->loss_cap = cap;
+  }
+  NRM_CUDA(nrm::launch_loss_scale(cf.data(), n, h->d_loss_counters, h->d_loss_counters + h->loss_cap, scale,
+                                  static_cast<cudaStream_t>(cuda_stream)),
+           "launch loss_scale_kernel");
+  return NRM_OK;
 }
 
 static int backward_batched(nrm_handle* h, const nrm_grad_frame* frames, int n, const float* scale,

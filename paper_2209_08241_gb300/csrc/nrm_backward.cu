@@ -25,6 +25,7 @@
 // bwd_batched_kernel covers a batch (grid = max tiles of a frame x frames).
 // Both are compiled for alpha = 1..4 as constants (shared-memory offsets and
 // loop steps become immediates) and once for any alpha.
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -305,7 +306,67 @@ cudaError_t set_smem(const void* fn, unsigned bytes) {
   return e;
 }
 
+// The per-frame factor of the cosine loss, scale = -1 / max(N_valid, 1), with
+// N_valid the number of nonzero mask bytes of the frame: kCountBlocks blocks
+// per frame count rows y = blockIdx.x, blockIdx.x + kCountBlocks, ...; each
+// block adds its count to the frame's counter, and the last block of the frame
+// to finish (the ordering of a fence and an atomic ticket) writes the scale
+// and returns both counters to zero for the next call. Integer sums: the
+// result does not depend on the order.
+constexpr int kCountBlocks = 32;
+constexpr int kCountThreads = 256;
+
+struct CountArgs {
+  LossCountFrame f[kLossCountMaxFrames];
+};
+
+__global__ void __launch_bounds__(kCountThreads)
+    loss_scale_kernel(const __grid_constant__ CountArgs a, unsigned* __restrict__ counts,
+                      unsigned* __restrict__ tickets, float* __restrict__ scale) {
+  NRM_DEBUG_ENTRY(nullptr);
+  const int f = (int)blockIdx.y;
+  const LossCountFrame fr = a.f[f];
+  unsigned c = 0;
+  for (int y = blockIdx.x; y < fr.H; y += gridDim.x) {
+    const uint8_t* row = fr.valid + (long long)y * fr.pitch;
+    for (int x = threadIdx.x; x < fr.W; x += kCountThreads) c += __ldg(row + x) != 0 ? 1u : 0u;
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  __shared__ unsigned part[kCountThreads / 32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = 0;
+    for (int w = 0; w < kCountThreads / 32; ++w) t += part[w];
+    atomicAdd(counts + f, t);
+    __threadfence();
+    if (atomicAdd(tickets + f, 1u) == gridDim.x - 1) {
+      const unsigned total = atomicExch(counts + f, 0u);
+      atomicExch(tickets + f, 0u);
+      scale[f] = -1.0f / (float)(total > 0 ? total : 1u);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_loss_scale(const LossCountFrame* frames, int n, unsigned* counts, unsigned* tickets, float* scale,
+                              cudaStream_t stream) {
+  for (int first = 0; first < n; first += kLossCountMaxFrames) {
+    const int m = std::min(kLossCountMaxFrames, n - first);
+    CountArgs a;
+    std::memset(&a, 0, sizeof(a));
+    std::memcpy(a.f, frames + first, sizeof(LossCountFrame) * (size_t)m);
+    unsigned* c = counts + first;
+    unsigned* t = tickets + first;
+    float* sc = scale + first;
+    void* args[4] = {&a, &c, &t, &sc};
+    cudaError_t e = cudaLaunchKernel((const void*)loss_scale_kernel, dim3(kCountBlocks, m), dim3(kCountThreads), args,
+                                     0, stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 unsigned bwd_smem_bytes(int alpha) {
   return depth_tile_bytes(alpha) + weight_tile_bytes(alpha) + mask_tile_bytes(alpha) + coord_table_bytes(alpha) + 16;

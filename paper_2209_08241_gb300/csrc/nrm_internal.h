@@ -193,6 +193,18 @@ cudaError_t launch_backward(const FrameDesc& fd, const BwdMaps& maps, const Glob
 // block is in device memory.
 cudaError_t launch_backward_batched(const BwdBatchArgs& args, int n_frames, int max_tiles, const Globals& g,
                                     cudaStream_t stream, const float* scale = nullptr);
+// One frame's mask for the cosine-loss factor (nrm_cosine_loss_scale).
+struct LossCountFrame {
+  const uint8_t* valid;
+  int H, W;
+  long long pitch;
+};
+constexpr int kLossCountMaxFrames = 128;  // frames per launch (the records travel as the kernel parameter)
+// scale[i] = -1 / max(N_valid(i), 1) for frames[0..n) (host array); counts and
+// tickets: n zeroed device words each, returned to zero by the kernel.
+cudaError_t launch_loss_scale(const LossCountFrame* frames, int n, unsigned* counts, unsigned* tickets, float* scale,
+                              cudaStream_t stream);
+
 // The same for at most kBwdParamMaxFrames frames with the records and maps
 // (host arrays) passed as one kernel parameter: no upload, no fences.
 constexpr int kBwdParamMaxFrames = 60;

@@ -240,3 +240,31 @@ def test_scaled_adjoint_rejects_missing_scale():
     rc = b.lib.nrm_backward_batched_scaled(b.h, arr, 1, None, None)
     assert rc == _lib.NRM_ERR_INVALID_ARG
     b.sync_status()
+
+
+def test_cosine_loss_scale_counts_every_mask():
+    """-1 / max(N_valid, 1) per frame from the masks, equal bit for bit to the
+    same expression in float32: mixed sizes and pitches, an empty frame, an
+    all-invalid frame, more than one launch's 128 frames, and repeated calls
+    (the handle's counters return to zero)."""
+    b = nrm.BatchedEstimator(nrm.NormalParams())
+    for n in (3, 140, 5):
+        items, gs, ms = [], [], []
+        for i in range(n):
+            W, H = [(97, 61), (640, 480), (0, 0), (130, 64), (5, 9)][i % 5]
+            d = torch.rand((H, W), device=DEV) + 1.0
+            K = (100.0, 100.0, W / 2, H / 2)
+            items.append((d, K))
+            gs.append(torch.zeros((H, W + 3, 4), device=DEV)[:, :W])  # grad_normals and mask share a pitch
+            mw = torch.zeros((H, W + 3), dtype=torch.uint8, device=DEV)
+            if i % 7 != 3:
+                mw[:, :W] = (torch.rand((H, W), device=DEV) > 0.3).to(torch.uint8) * (1 + i % 3)
+            ms.append(mw[:, :W])
+        arr, _ = b.make_grad_frames(items, gs, ms)
+        for _ in range(2):
+            scale = b.cosine_loss_scale(arr, n)
+            torch.cuda.synchronize()
+            counts = torch.stack([(m != 0).sum(dtype=torch.float32) for m in ms])
+            ref = -1.0 / counts.clamp(min=1.0)
+            assert torch.equal(scale, ref.to(torch.float32)), n
+    b.sync_status()
