@@ -6,7 +6,7 @@ call, every byte outside the logical output must still hold the sentinel.
 Covered: the plain and batched forward (float4, half4 and octahedral outputs,
 point clouds, float32 and uint16 input, ragged sizes, aligned and unaligned
 pitches, parameter-block and descriptor-ring batches), the multi-scale
-variant, the adjoint (plain, batched, scaled), plane fitting, the evaluation
+variant, the adjoint (plain, batched, scaled) and the loss scale, plane fitting, the evaluation
 kernels, the allocation-free entry point and the host-buffer path."""
 
 import pytest
@@ -166,6 +166,9 @@ def test_adjoint_guard_bands():
         b.run_backward_scaled(arr, nfr, scale)
         for i, gp in enumerate(guards):
             gp.check(f"scaled adjoint frame {i} of {nfr}")
+        sg = Guarded(1, nfr, torch.float32)
+        b.cosine_loss_scale(arr, nfr, sg.view[0])
+        sg.check(f"cosine loss scale of {nfr} frames")
     b.sync_status()
 
 
