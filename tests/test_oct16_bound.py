@@ -41,3 +41,15 @@ def test_round_trip_within_the_tolerance():
     assert ang.max() <= ANG_TOL_OCT16
     assert ang.max() <= math.sqrt(6) / 32767
     assert ang.max() > 1e-6  # the quantisation is really exercised
+
+
+def test_half_output_rounding_within_its_tolerance():
+    """The half4 tolerance (5e-3 rad): a unit normal rounded to float16 per
+    component turns by at most ~sqrt(3) 2^-11 (about 8.5e-4 rad)."""
+    from parity import ANG_TOL_F16
+    rng = np.random.default_rng(12)
+    v = rng.normal(size=(400000, 3))
+    v /= np.linalg.norm(v, axis=-1, keepdims=True)
+    h = v.astype(np.float16).astype(np.float64)
+    ang = _angles(h / np.linalg.norm(h, axis=-1, keepdims=True), v)
+    assert ang.max() <= math.sqrt(3) * 2.0 ** -11 <= ANG_TOL_F16
