@@ -4,7 +4,8 @@ diagonals, at the poles and on the equator) encoded exactly in FP64 from the
 published definition (project onto |x| + |y| + |z| = 1, fold the lower half,
 round 32767 p to the nearest integer) and decoded with the tests' decoder
 come back within ANG_TOL_OCT16, and the worst case found stays within the
-analytic bound sqrt(6)/32767. CPU only."""
+analytic bound sqrt(6)/32767. The half-output tolerance is pinned the same
+way against float16 rounding. CPU only."""
 import math
 
 import numpy as np
